@@ -1,0 +1,270 @@
+"""Seeded synthetic graph inputs shared by the CPU oracle and the CUDA path.
+
+This package only makes inputs (CSR arrays, weights, sources).  It holds none
+of the traversal arithmetic; the oracle and the CUDA library both consume its
+output and neither is imported here.
+
+Large graphs come from the C builder in ``graphgen.c`` (OpenMP, counter-based
+SplitMix64 streams, so results do not depend on the thread count); tiny
+hand-made graphs come from :func:`csr_from_edges`.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "graphgen.c")
+_SO = os.path.join(_HERE, "_graphgen.so")
+_lib_handle = None
+
+KRON = 0
+UNIFORM = 1
+
+
+def build_lib(force: bool = False) -> str:
+    """Compile graphgen.c into _graphgen.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O3", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _lib():
+    global _lib_handle
+    if _lib_handle is None:
+        lib = ctypes.CDLL(build_lib())
+        u64, i32 = ctypes.c_uint64, ctypes.c_int
+        p = ctypes.c_void_p
+        lib.gg_rand.restype = u64
+        lib.gg_rand.argtypes = [u64, u64]
+        lib.gg_perm.argtypes = [u64, u64, p]
+        lib.gg_sample.argtypes = [i32, u64, i32, u64, p, u64, u64, p, p]
+        lib.gg_count.argtypes = [i32, u64, i32, u64, p, u64, p]
+        lib.gg_fill.argtypes = [i32, u64, i32, u64, p, u64, p, p, p, p]
+        lib.gg_compact.argtypes = [u64, p, p, p, p]
+        lib.gg_weights.argtypes = [u64, p, p, u64, p]
+        lib.gg_num_threads.restype = i32
+        _lib_handle = lib
+    return _lib_handle
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def aligned_empty(count: int, dtype, align: int = 4096) -> np.ndarray:
+    """Uninitialised 1-D array whose data pointer is `align`-byte aligned."""
+    dtype = np.dtype(dtype)
+    nbytes = max(1, int(count)) * dtype.itemsize
+    raw = np.empty(nbytes + align, dtype=np.uint8)
+    off = (-raw.ctypes.data) % align
+    return raw[off:off + nbytes].view(dtype)[:int(count)]
+
+
+@dataclass
+class Graph:
+    """A CSR graph: offsets uint64[n+1], cols uint64[m], optional weights uint32[m]."""
+    n: int
+    offsets: np.ndarray
+    cols: np.ndarray
+    weights: Optional[np.ndarray] = None
+    undirected: bool = True
+    name: str = ""
+
+    @property
+    def m(self) -> int:
+        return int(self.offsets[-1])
+
+    def degrees(self) -> np.ndarray:
+        return np.diff(self.offsets).astype(np.int64)
+
+
+def rand(seed: int, i: int) -> int:
+    """i-th output of the SplitMix64 stream seeded with `seed`."""
+    return int(_lib().gg_rand(seed & (2**64 - 1), i))
+
+
+def permutation(n: int, seed: int) -> np.ndarray:
+    perm = np.empty(n, dtype=np.uint64)
+    _lib().gg_perm(n, seed, _ptr(perm))
+    return perm
+
+
+def samples(kind: int, n: int, scale: int, seed: int, count: int, permute: bool = True,
+            k0: int = 0):
+    """Raw edge samples (before cleaning) of a generated graph."""
+    perm = permutation(n, seed) if (kind == KRON and permute) else None
+    src = np.empty(count, dtype=np.uint64)
+    dst = np.empty(count, dtype=np.uint64)
+    _lib().gg_sample(kind, n, scale, seed, _ptr(perm), k0, count, _ptr(src), _ptr(dst))
+    return src, dst
+
+
+def _build(kind: int, n: int, scale: int, nsamples: int, seed: int, permute: bool,
+           with_weights: bool, wseed: int, name: str) -> Graph:
+    lib = _lib()
+    perm = permutation(n, seed) if (kind == KRON and permute) else None
+    deg = np.zeros(n, dtype=np.uint64)
+    lib.gg_count(kind, n, scale, seed, _ptr(perm), nsamples, _ptr(deg))
+    off_raw = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(deg, out=off_raw[1:])
+    m_raw = int(off_raw[-1])
+    cols = aligned_empty(m_raw, np.uint64)
+    cursor = np.empty(n, dtype=np.uint64)
+    lib.gg_fill(kind, n, scale, seed, _ptr(perm), nsamples, _ptr(off_raw), _ptr(cursor),
+                _ptr(cols), _ptr(deg))
+    del cursor
+    off = np.empty(n + 1, dtype=np.uint64)
+    lib.gg_compact(n, _ptr(off_raw), _ptr(deg), _ptr(cols), _ptr(off))
+    m = int(off[-1])
+    cols = cols[:m]
+    w = None
+    if with_weights:
+        w = aligned_empty(m, np.uint32)
+        lib.gg_weights(n, _ptr(off), _ptr(cols), wseed, _ptr(w))
+    return Graph(n=n, offsets=off, cols=cols, weights=w, undirected=True, name=name)
+
+
+def kronecker(scale: int, edge_factor: int, seed: int = 1, weights: bool = False,
+              wseed: Optional[int] = None, permute: bool = True) -> Graph:
+    """Undirected Kronecker graph: 2^scale vertices, edge_factor * 2^scale samples,
+    initiator (0.57, 0.19, 0.19, 0.05), ids permuted by seed, cleaned, symmetric."""
+    n = 1 << scale
+    return _build(KRON, n, scale, edge_factor * n, seed, permute, weights,
+                  seed if wseed is None else wseed, f"kron{scale}_ef{edge_factor}_s{seed}")
+
+
+def uniform(n: int, avg_degree: float, seed: int = 1, weights: bool = False,
+            wseed: Optional[int] = None) -> Graph:
+    """Undirected uniform-random graph with n vertices and n*avg_degree/2 samples
+    (so about n*avg_degree directed edges after symmetrisation)."""
+    nsamples = int(round(n * avg_degree / 2))
+    return _build(UNIFORM, n, 0, nsamples, seed, False, weights,
+                  seed if wseed is None else wseed, f"urand_n{n}_d{avg_degree}_s{seed}")
+
+
+def add_weights(g: Graph, seed: int = 1) -> Graph:
+    """Attach symmetric weights in [1, 255] to an existing graph."""
+    w = aligned_empty(g.m, np.uint32)
+    if g.m:
+        _lib().gg_weights(g.n, _ptr(np.ascontiguousarray(g.offsets, dtype=np.uint64)),
+                          _ptr(np.ascontiguousarray(g.cols, dtype=np.uint64)), seed, _ptr(w))
+    g.weights = w
+    return g
+
+
+def csr_from_edges(n: int, src, dst, weights=None, symmetrize: bool = True,
+                   dedup: bool = True, drop_self_loops: bool = True, sort: bool = True,
+                   name: str = "") -> Graph:
+    """Build a CSR graph from an edge list with numpy (small graphs).
+
+    With dedup, duplicate (u, v) pairs keep the smallest weight.  Without
+    dedup/sort, rows keep the input order (stable), which tests use to make
+    lists with duplicates and self-loops.
+    """
+    src = np.asarray(src, dtype=np.uint64).ravel()
+    dst = np.asarray(dst, dtype=np.uint64).ravel()
+    w = None if weights is None else np.asarray(weights, dtype=np.uint32).ravel()
+    if drop_self_loops:
+        keep = src != dst
+        src, dst = src[keep], dst[keep]
+        w = None if w is None else w[keep]
+    if symmetrize:
+        src, dst = np.concatenate([src, dst]), np.concatenate([dst, src])
+        w = None if w is None else np.concatenate([w, w])
+    if sort or dedup:
+        if w is None:
+            order = np.lexsort((dst, src))
+        else:
+            order = np.lexsort((w, dst, src))
+        src, dst = src[order], dst[order]
+        w = None if w is None else w[order]
+    else:
+        order = np.argsort(src, kind="stable")
+        src, dst = src[order], dst[order]
+        w = None if w is None else w[order]
+    if dedup and src.size:
+        keep = np.ones(src.size, dtype=bool)
+        keep[1:] = (src[1:] != src[:-1]) | (dst[1:] != dst[:-1])
+        src, dst = src[keep], dst[keep]
+        w = None if w is None else w[keep]
+    deg = np.bincount(src.astype(np.int64), minlength=n).astype(np.uint64) if src.size else \
+        np.zeros(n, dtype=np.uint64)
+    off = np.zeros(n + 1, dtype=np.uint64)
+    np.cumsum(deg, out=off[1:])
+    cols = aligned_empty(dst.size, np.uint64)
+    cols[:] = dst
+    wa = None
+    if w is not None:
+        wa = aligned_empty(w.size, np.uint32)
+        wa[:] = w
+    return Graph(n=n, offsets=off, cols=cols, weights=wa, undirected=symmetrize, name=name)
+
+
+def path_graph(n: int) -> Graph:
+    i = np.arange(max(n - 1, 0), dtype=np.uint64)
+    return csr_from_edges(n, i, i + 1, name=f"path{n}")
+
+
+def star_graph(n: int, center: int = 0) -> Graph:
+    leaves = np.array([v for v in range(n) if v != center], dtype=np.uint64)
+    return csr_from_edges(n, np.full(leaves.size, center, dtype=np.uint64), leaves,
+                          name=f"star{n}")
+
+
+def complete_graph(n: int) -> Graph:
+    iu = np.triu_indices(n, 1)
+    return csr_from_edges(n, iu[0], iu[1], name=f"complete{n}")
+
+
+def empty_graph(n: int) -> Graph:
+    return csr_from_edges(n, np.zeros(0), np.zeros(0), name=f"empty{n}")
+
+
+def random_small(n: int, p: float, seed: int, directed: bool = False) -> Graph:
+    """Erdos-Renyi G(n, p) from the counter stream (small n only)."""
+    s, d = [], []
+    k = 0
+    for u in range(n):
+        for v in range(n):
+            if u == v or (not directed and v < u):
+                continue
+            r = rand(seed, k) >> 11
+            k += 1
+            if r < int(p * 2**53):
+                s.append(u)
+                d.append(v)
+    return csr_from_edges(n, np.array(s, dtype=np.uint64), np.array(d, dtype=np.uint64),
+                          symmetrize=not directed, name=f"gnp{n}_{p}_{seed}")
+
+
+def max_degree_vertex(g: Graph) -> int:
+    """Highest-degree vertex; ties go to the smallest id."""
+    return int(np.argmax(g.degrees())) if g.n else 0
+
+
+def random_sources(g: Graph, count: int, seed: int = 2, min_degree: int = 1) -> np.ndarray:
+    """`count` distinct seeded vertices with out-degree >= min_degree."""
+    deg = g.degrees()
+    cand = np.nonzero(deg >= min_degree)[0]
+    if cand.size == 0:
+        return np.zeros(0, dtype=np.uint64)
+    out, seen, i = [], set(), 0
+    while len(out) < min(count, cand.size):
+        j = int(cand[(rand(seed, i) * cand.size) >> 64])
+        i += 1
+        if j not in seen:
+            seen.add(j)
+            out.append(j)
+    return np.array(out, dtype=np.uint64)
+
+
+def num_threads() -> int:
+    return int(_lib().gg_num_threads())

@@ -1,0 +1,90 @@
+"""The seeded input generators: structure, cleaning and determinism."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+import graphgen as gg
+
+
+def _check_clean_symmetric(g):
+    deg = g.degrees()
+    src = np.repeat(np.arange(g.n, dtype=np.uint64), deg)
+    assert np.all(src != g.cols)  # no self-loops
+    assert np.all(g.cols < g.n)
+    # rows strictly increasing => sorted and de-duplicated
+    inner = np.ones(g.m, dtype=bool)
+    starts = g.offsets[:-1][deg > 0].astype(np.int64)
+    inner[starts] = False
+    assert np.all(np.diff(g.cols.astype(np.int64))[inner[1:]] > 0)
+    # symmetric: the multiset of (u, v) equals that of (v, u)
+    a = np.sort(src * np.uint64(g.n) + g.cols)
+    b = np.sort(g.cols * np.uint64(g.n) + src)
+    assert np.array_equal(a, b)
+
+
+def test_kronecker_clean_symmetric_weighted():
+    g = gg.kronecker(12, 16, seed=1, weights=True)
+    assert g.n == 4096
+    _check_clean_symmetric(g)
+    assert 0 < g.m <= 2 * 16 * 4096
+    assert g.weights.min() >= 1 and g.weights.max() <= 255
+    # weight symmetry: w(u,v) == w(v,u)
+    deg = g.degrees()
+    src = np.repeat(np.arange(g.n, dtype=np.uint64), deg)
+    key_uv = src * np.uint64(g.n) + g.cols
+    key_vu = g.cols * np.uint64(g.n) + src
+    o1, o2 = np.argsort(key_uv), np.argsort(key_vu)
+    assert np.array_equal(g.weights[o1], g.weights[o2])
+    # heavy tail: the hub is far above the mean degree
+    assert deg.max() > 20 * deg.mean()
+
+
+def test_uniform_degree_distribution():
+    g = gg.uniform(1 << 16, 32, seed=1)
+    _check_clean_symmetric(g)
+    deg = g.degrees()
+    assert abs(deg.mean() - 32) < 0.5
+    assert deg.max() < 80
+
+
+def test_generation_is_deterministic_across_thread_counts():
+    code = ("import graphgen as gg, hashlib;"
+            "g = gg.kronecker(11, 8, seed=3, weights=True);"
+            "print(hashlib.sha1(g.offsets.tobytes() + g.cols.tobytes() + g.weights.tobytes()).hexdigest())")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for t in ("1", "3"):
+        env = dict(os.environ, OMP_NUM_THREADS=t, PYTHONPATH=root)
+        outs.append(subprocess.check_output([sys.executable, "-c", code], env=env, cwd=root).strip())
+    assert outs[0] == outs[1]
+
+
+def test_seeds_differ_and_permutation_is_bijective():
+    p = gg.permutation(1000, 5)
+    assert np.array_equal(np.sort(p), np.arange(1000, dtype=np.uint64))
+    a = gg.kronecker(10, 8, seed=1)
+    b = gg.kronecker(10, 8, seed=2)
+    assert not np.array_equal(a.cols[:100], b.cols[:100])
+
+
+def test_sources():
+    g = gg.kronecker(10, 8, seed=1)
+    s = gg.max_degree_vertex(g)
+    assert g.degrees()[s] == g.degrees().max()
+    assert s == int(np.nonzero(g.degrees() == g.degrees().max())[0][0])
+    r = gg.random_sources(g, 16, seed=2)
+    assert len(set(r.tolist())) == 16 and np.all(g.degrees()[r.astype(np.int64)] >= 1)
+
+
+def test_csr_from_edges_keeps_duplicates_when_asked():
+    g = gg.csr_from_edges(3, [0, 0, 1, 2], [1, 1, 1, 0], symmetrize=False, dedup=False,
+                          drop_self_loops=False, sort=False)
+    assert g.offsets.tolist() == [0, 2, 3, 4]
+    assert g.cols.tolist() == [1, 1, 1, 0]
+
+
+def test_aligned_allocation():
+    a = gg.aligned_empty(1000, np.uint64, 4096)
+    assert a.ctypes.data % 4096 == 0 and a.size == 1000
