@@ -1,0 +1,198 @@
+/*
+ * emogi.h - C ABI of the GB300 zero-copy graph-traversal library.
+ *
+ * The library runs level-synchronous BFS, SSSP and connected components over
+ * a CSR graph whose edge (and weight) arrays may stay in pinned host memory
+ * and are read by the GPU in place ("zero-copy", paper Sec. 3) with merged,
+ * 128-byte-aligned warp accesses (Sec. 4.3), while the vertex list and all
+ * vertex state live in GPU memory (Sec. 4.2).  Everything on the traversal
+ * path runs in the library's own CUDA kernels (sm_103a); there is no CPU
+ * fallback.
+ *
+ * Conventions shared by every entry point
+ *  - Vertex ids at the API are uint64_t; the library requires
+ *    n < 2^32 - 1 so that per-vertex state fits in uint32_t.
+ *  - "Unreachable" / "no value" is UINT32_MAX (EMOGI_INF).
+ *  - Calls are synchronous: when a call returns EMOGI_OK its outputs are
+ *    complete (device outputs included).  A graph handle may be used by one
+ *    thread at a time; distinct handles may be used concurrently.
+ *  - No C++ exception crosses this boundary.  Every entry point returns an
+ *    emogi_status; on failure emogi_last_error() returns a thread-local,
+ *    human-readable description that stays valid until the next call on the
+ *    same thread.  CUDA runtime failures map to EMOGI_E_CUDA.
+ *  - Host arrays are read during the call only and never retained, except
+ *    with EMOGI_LOAD_BORROW (see emogi_load_csr).
+ */
+#ifndef EMOGI_H
+#define EMOGI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EMOGI_INF 0xFFFFFFFFu
+#define EMOGI_MAX_SOURCES 64u
+
+typedef struct emogi_graph_s* emogi_graph;
+
+typedef enum {
+    EMOGI_OK = 0,
+    EMOGI_E_ARG = 1,         /* invalid argument (bad CSR, source out of range, NULL pointer, ...) */
+    EMOGI_E_NOMEM = 2,       /* a host or device allocation failed */
+    EMOGI_E_BUDGET = 3,      /* the device-memory budget (emogi_set_device_budget) would be exceeded */
+    EMOGI_E_CUDA = 4,        /* a CUDA runtime call or kernel launch failed */
+    EMOGI_E_TIMEOUT = 5,     /* a bounded device-side wait gave up (persistent kernels) */
+    EMOGI_E_OVERFLOW = 6,    /* a shortest-path distance does not fit below UINT32_MAX */
+    EMOGI_E_UNSUPPORTED = 7  /* operation not defined for this graph (e.g. CC on a directed graph) */
+} emogi_status;
+
+/* Where the edge list (col_idx) and the weights live.  The row offsets and all
+ * vertex state are always in GPU memory (Sec. 4.2). */
+typedef enum {
+    EMOGI_PLACE_DEVICE = 0,  /* copied into GPU memory (all-in-HBM reference point) */
+    EMOGI_PLACE_HOST = 1,    /* pinned, mapped host memory read zero-copy (Sec. 3.1, the EMOGI case) */
+    EMOGI_PLACE_MANAGED = 2  /* cudaMallocManaged + ReadMostly advice: the UVM baseline (Sec. 5.1.2 (a)) */
+} emogi_placement;
+
+/* emogi_load_csr flags */
+enum {
+    EMOGI_LOAD_UNDIRECTED = 1u << 0, /* caller asserts the CSR is symmetric; required by emogi_cc */
+    EMOGI_LOAD_BORROW = 1u << 1      /* HOST only: pin and map the caller's arrays in place, no copy */
+};
+
+/* How a worker reads one neighbour list (Sec. 4.2, Sec. 4.3, Listings
+ * "Uncoalesced Memory Access" and "Coalesced Memory Access (Merged + Aligned)"). */
+typedef enum {
+    EMOGI_ACCESS_MERGED_ALIGNED = 0, /* groups of lanes read the list from the 128-byte line that
+                                        contains its first element, 16 bytes per lane; lists longer
+                                        than a threshold are split across warps */
+    EMOGI_ACCESS_MERGED = 1,         /* one warp per vertex, 8 bytes per lane, from the list's own
+                                        (unaligned) start: the paper's "Merged" variant */
+    EMOGI_ACCESS_NAIVE = 2           /* one thread per vertex walking its list element by element:
+                                        the paper's "Naive" variant */
+} emogi_access;
+
+/* emogi_opts.flags */
+enum {
+    EMOGI_OPT_TIME_KERNELS = 1u << 0 /* bracket every neighbour-expansion launch with CUDA events and
+                                        report their summed duration in emogi_stats.expand_ms */
+};
+
+/* Per-call options.  Pass NULL for defaults.  struct_size must be
+ * sizeof(emogi_opts) so that the struct can grow. */
+typedef struct {
+    uint32_t struct_size;
+    uint32_t access;       /* emogi_access; default EMOGI_ACCESS_MERGED_ALIGNED */
+    uint32_t granularity;  /* lanes per vertex for MERGED_ALIGNED: 4, 8, 16 or 32; 0 = automatic */
+    uint32_t chunk_lines;  /* 128-byte lines per work item for split (long) lists; 0 = automatic */
+    uint64_t timeout_ns;   /* bound on device-side waits of persistent kernels; 0 = 2 s */
+    void* cuda_stream;     /* cudaStream_t to run on; NULL = the graph's own stream */
+    int32_t out_on_device; /* 1: output pointers are device pointers of the current device */
+    uint32_t flags;        /* EMOGI_OPT_* */
+} emogi_opts;
+
+/* Per-call statistics (optional output). */
+typedef struct {
+    uint32_t iterations;    /* levels (BFS), relaxation rounds (SSSP), edge passes (CC) */
+    uint32_t reserved;
+    uint64_t edges_scanned; /* neighbour-list entries read by the expansion kernels */
+    uint64_t edges_reached; /* sum of out-degrees of reached vertices (the TEPS numerator; m for CC) */
+    uint64_t edge_bytes;    /* edges_scanned * 8 */
+    uint64_t weight_bytes;  /* weights read (SSSP): edges_scanned * 4 */
+    double ms;              /* device time of the traversal, CUDA events on the launch stream */
+    double expand_ms;       /* with EMOGI_OPT_TIME_KERNELS: summed duration of expansion launches */
+    uint64_t expand_launches; /* neighbour-expansion sweeps */
+    uint64_t kernel_launches; /* every kernel the call launched */
+} emogi_stats;
+
+/* Load a CSR graph (Sec. 2.1, Figure "Sample undirected graph and its CSR
+ * representation"; placement as in Sec. 3.1 and Sec. 4.2).
+ *   n            number of vertices, 0 <= n < 2^32 - 1
+ *   m            number of stored (directed) edges
+ *   row_offsets  host uint64_t[n+1], non-decreasing, row_offsets[0] == 0,
+ *                row_offsets[n] == m; copied to GPU memory
+ *   col_idx      host uint64_t[m], every entry < n; duplicates and self-loops
+ *                are allowed
+ *   weights      host uint32_t[m] or NULL (SSSP needs weights)
+ *   place        emogi_placement of col_idx and weights
+ *   flags        EMOGI_LOAD_* bits
+ *   out          receives the handle; release it with emogi_free_graph
+ * With EMOGI_LOAD_BORROW (HOST only) the library registers col_idx and weights
+ * with cudaHostRegister instead of copying; they must be 16-byte aligned and
+ * the caller must keep them alive and unchanged until emogi_free_graph.
+ * Errors: EMOGI_E_ARG (invalid CSR or flags), EMOGI_E_BUDGET, EMOGI_E_NOMEM,
+ * EMOGI_E_CUDA.  On error *out is set to NULL and nothing is retained. */
+emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets,
+                            const uint64_t* col_idx, const uint32_t* weights,
+                            emogi_placement place, uint32_t flags, emogi_graph* out);
+
+/* Breadth-first search from src (Sec. 2.1, Algorithm "High-level Graph
+ * Traversal Flow" with the BFS condition: an unvisited neighbour of an active
+ * vertex becomes active at the next depth; one kernel round per level, Sec. 4.2).
+ *   level  uint32_t[n] output (host, or device if opts->out_on_device):
+ *          level[src] = 0, hop distance for reached vertices, EMOGI_INF otherwise.
+ * Errors: EMOGI_E_ARG (src >= n, NULL pointer), EMOGI_E_BUDGET, EMOGI_E_NOMEM,
+ * EMOGI_E_CUDA.  The output is unspecified on error. */
+emogi_status emogi_bfs(emogi_graph g, uint64_t src, uint32_t* level, const emogi_opts* opts,
+                       emogi_stats* stats);
+
+/* Single-source shortest paths with the graph's uint32 weights (Sec. 5.1.2,
+ * Sec. 5.4: SSSP reads each weight beside its edge).  Frontier-based
+ * Bellman-Ford: active vertices relax their out-edges with an atomic minimum
+ * and improved vertices become active, until no distance changes.
+ *   dist   uint32_t[n] output: exact shortest distance, EMOGI_INF if unreachable.
+ * Errors: as emogi_bfs, plus EMOGI_E_UNSUPPORTED (graph loaded without
+ * weights) and EMOGI_E_OVERFLOW (a finite distance >= UINT32_MAX). */
+emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi_opts* opts,
+                        emogi_stats* stats);
+
+/* Connected components of an undirected graph (Sec. 5.4: every vertex starts
+ * active and the entire edge list is streamed).  One pass over all edges
+ * hooks the larger union-find root under the smaller with compare-and-swap,
+ * then pointer jumping resolves every vertex to its root.
+ *   label  uint32_t[n] output: the smallest vertex id of the vertex's component.
+ * Errors: EMOGI_E_UNSUPPORTED if the graph was not loaded with
+ * EMOGI_LOAD_UNDIRECTED (the paper runs CC on undirected graphs only), and
+ * the errors of emogi_bfs. */
+emogi_status emogi_cc(emogi_graph g, uint32_t* label, const emogi_opts* opts, emogi_stats* stats);
+
+/* Set the device-memory budget in bytes for all graphs and work buffers the
+ * library allocates from now on (0 = unlimited).  Allocations that would
+ * exceed it fail with EMOGI_E_BUDGET.  Mirrors the paper's GPU memory cap of
+ * its A100 runs (Sec. 5.6).  Returns EMOGI_OK. */
+emogi_status emogi_set_device_budget(uint64_t bytes);
+
+/* Bytes of device memory the library currently holds (graphs + work buffers). */
+uint64_t emogi_device_bytes_in_use(void);
+
+/* Release a graph and every buffer the library holds for it.  NULL is a no-op.
+ * Returns EMOGI_E_CUDA if a CUDA free failed (the handle is released anyway). */
+emogi_status emogi_free_graph(emogi_graph g);
+
+/* Properties of a loaded graph. */
+uint64_t emogi_graph_num_vertices(emogi_graph g);
+uint64_t emogi_graph_num_edges(emogi_graph g);
+int emogi_graph_placement(emogi_graph g);
+
+/* Static description of a status code. */
+const char* emogi_status_string(emogi_status s);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* emogi_last_error(void);
+
+/* Library version string. */
+const char* emogi_version(void);
+
+/* Testing hook: make the k-th device allocation from now on (k >= 1) fail as
+ * if cudaMalloc had returned out-of-memory; 0 disarms.  Lets tests exercise
+ * EMOGI_E_NOMEM handling without exhausting a real GPU. */
+void emogi_test_fail_device_alloc_after(int k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EMOGI_H */

@@ -1,0 +1,410 @@
+// Graph loading and placement (paper Sec. 3.1 "Enabling Zero-Copy", Sec. 4.2
+// "EMOGI Baseline", Sec. 5.1.2 (a) for the UVM baseline), the device-memory
+// budget, work buffers and the status/error plumbing of the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.h"
+
+namespace emogi {
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string t_last_error;
+
+void set_error(const std::string& msg) { t_last_error = msg; }
+void clear_error() { t_last_error.clear(); }
+
+emogi_status fail(emogi_status s, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_last_error = std::string(emogi_status_string(s)) + ": " + buf;
+    return s;
+}
+
+// ---------------------------------------------------------------- budget
+static std::atomic<uint64_t> g_budget{0};
+static std::atomic<uint64_t> g_in_use{0};
+static std::atomic<int> g_fail_after{0};
+
+emogi_status dev_alloc(void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    uint64_t budget = g_budget.load();
+    uint64_t prev = g_in_use.fetch_add(bytes);
+    if (budget && prev + bytes > budget) {
+        g_in_use.fetch_sub(bytes);
+        return fail(EMOGI_E_BUDGET, "%s needs %zu bytes, %llu of %llu budget bytes already in use",
+                    what, bytes, (unsigned long long)prev, (unsigned long long)budget);
+    }
+    int k = g_fail_after.load();
+    if (k > 0) {
+        if (g_fail_after.fetch_sub(1) == 1) {
+            g_in_use.fetch_sub(bytes);
+            return fail(EMOGI_E_NOMEM, "%s: injected device allocation failure", what);
+        }
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        g_in_use.fetch_sub(bytes);
+        *p = nullptr;
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return fail(EMOGI_E_NOMEM, "%s: cudaMalloc(%zu) out of memory", what, bytes);
+        }
+        return fail(EMOGI_E_CUDA, "%s: cudaMalloc(%zu): %s", what, bytes, cudaGetErrorString(e));
+    }
+    return EMOGI_OK;
+}
+
+emogi_status dev_free(void* p, size_t bytes) {
+    if (!p) return EMOGI_OK;
+    if (bytes == 0) bytes = 16;
+    g_in_use.fetch_sub(bytes);
+    EMOGI_CUDA_TRY(cudaFree(p));
+    return EMOGI_OK;
+}
+
+int sm_count(int device) {
+    static std::mutex mu;
+    static std::vector<int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)cache.size() <= device) cache.resize(device + 1, 0);
+    if (!cache[device]) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device);
+        cache[device] = v > 0 ? v : 1;
+    }
+    return cache[device];
+}
+
+emogi_status parse_opts(const emogi_opts* in, Opts* o) {
+    *o = Opts();
+    if (!in) return EMOGI_OK;
+    if (in->struct_size < offsetof(emogi_opts, flags) + sizeof(uint32_t))
+        return fail(EMOGI_E_ARG, "emogi_opts.struct_size %u is smaller than this library's %zu",
+                    in->struct_size, sizeof(emogi_opts));
+    if (in->access > EMOGI_ACCESS_NAIVE) return fail(EMOGI_E_ARG, "unknown access mode %u", in->access);
+    if (in->granularity != 0 && in->granularity != 4 && in->granularity != 8 &&
+        in->granularity != 16 && in->granularity != 32)
+        return fail(EMOGI_E_ARG, "granularity must be 0, 4, 8, 16 or 32 (got %u)", in->granularity);
+    if (in->chunk_lines > (1u << 20)) return fail(EMOGI_E_ARG, "chunk_lines too large");
+    o->access = in->access;
+    o->granularity = in->granularity;
+    o->chunk_lines = in->chunk_lines;
+    if (in->timeout_ns) o->timeout_ns = in->timeout_ns;
+    o->stream = (cudaStream_t)in->cuda_stream;
+    o->out_on_device = in->out_on_device != 0;
+    o->flags = in->flags;
+    return EMOGI_OK;
+}
+
+// ---------------------------------------------------------------- work buffers
+emogi_status ensure_workspace(emogi_graph g) {
+    Workspace& ws = g->ws;
+    if (ws.ctr) return EMOGI_OK;
+    const uint64_t n = g->n ? g->n : 1;
+    ws.n = n;
+    // split-list vertices: a list is split when its aligned span exceeds 32
+    // lines (512 ids); the span starts at most 15 ids before the list, so a
+    // split list holds at least 498 ids and one sweep splits at most m / 498
+    ws.lq_cap = std::min<uint64_t>(n, g->m / 497 + 1);
+    struct Item { void** p; size_t bytes; const char* what; };
+    Item items[] = {
+        {(void**)&ws.q[0], n * 4, "frontier queue 0"},
+        {(void**)&ws.q[1], n * 4, "frontier queue 1"},
+        {(void**)&ws.state, n * 4, "vertex state"},
+        {(void**)&ws.flag, n * 4, "queued flags"},
+        {(void**)&ws.lq_v, ws.lq_cap * 4, "split-list vertices"},
+        {(void**)&ws.lq_base, ws.lq_cap * 8, "split-list chunk bases"},
+        {(void**)&ws.ctr, sizeof(DevCounters), "counters"},
+    };
+    for (auto& it : items) {
+        emogi_status s = dev_alloc(it.p, it.bytes, it.what);
+        if (s != EMOGI_OK) {
+            release_workspace(g);
+            return s;
+        }
+        ws.dev_bytes += it.bytes;
+    }
+    cudaError_t e = cudaHostAlloc((void**)&ws.h_ctr, sizeof(DevCounters), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaMemset(ws.flag, 0, n * 4);
+    for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&ws.ev[i]);
+    if (e != cudaSuccess) {
+        release_workspace(g);
+        return fail(EMOGI_E_CUDA, "work buffers: %s", cudaGetErrorString(e));
+    }
+    return EMOGI_OK;
+}
+
+void release_workspace(emogi_graph g) {
+    Workspace& ws = g->ws;
+    dev_free(ws.q[0], ws.n * 4);
+    dev_free(ws.q[1], ws.n * 4);
+    dev_free(ws.state, ws.n * 4);
+    dev_free(ws.flag, ws.n * 4);
+    dev_free(ws.lq_v, ws.lq_cap * 4);
+    dev_free(ws.lq_base, ws.lq_cap * 8);
+    dev_free(ws.ctr, sizeof(DevCounters));
+    // dev_free's accounting assumes the sizes it was allocated with; when a
+    // partial allocation failed, unallocated entries are null and skipped.
+    if (ws.h_ctr) cudaFreeHost(ws.h_ctr);
+    for (auto& e : ws.ev)
+        if (e) cudaEventDestroy(e);
+    ws = Workspace();
+}
+
+// ---------------------------------------------------------------- validation
+// Checks the CSR in parallel on the host: offsets monotone from 0 to m, every
+// column id below n.
+static emogi_status validate_csr(uint64_t n, uint64_t m, const uint64_t* off, const uint64_t* cols) {
+    if (off[0] != 0) return fail(EMOGI_E_ARG, "row_offsets[0] = %llu, expected 0", (unsigned long long)off[0]);
+    if (off[n] != m)
+        return fail(EMOGI_E_ARG, "row_offsets[n] = %llu but m = %llu", (unsigned long long)off[n],
+                    (unsigned long long)m);
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    std::atomic<uint64_t> bad_row{UINT64_MAX}, bad_col{UINT64_MAX};
+    auto work = [&](unsigned t) {
+        uint64_t r0 = n * t / nt, r1 = n * (t + 1) / nt;
+        for (uint64_t v = r0; v < r1; v++)
+            if (off[v + 1] < off[v]) { bad_row = v; return; }
+        uint64_t c0 = m * t / nt, c1 = m * (t + 1) / nt;
+        for (uint64_t i = c0; i < c1; i++)
+            if (cols[i] >= n) { bad_col = i; return; }
+    };
+    if ((uint64_t)nt * 65536 > m + n) nt = 1;
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nt; t++) th.emplace_back(work, t);
+    work(0);
+    for (auto& x : th) x.join();
+    if (bad_row != UINT64_MAX)
+        return fail(EMOGI_E_ARG, "row_offsets decrease at vertex %llu", (unsigned long long)bad_row.load());
+    if (bad_col != UINT64_MAX)
+        return fail(EMOGI_E_ARG, "col_idx[%llu] = %llu is not below n = %llu", (unsigned long long)bad_col.load(),
+                    (unsigned long long)cols[bad_col.load()], (unsigned long long)n);
+    return EMOGI_OK;
+}
+
+static void parallel_copy(void* dst, const void* src, size_t bytes) {
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (bytes < (64u << 20)) nt = 1;
+    std::vector<std::thread> th;
+    auto work = [&](unsigned t) {
+        size_t a = bytes * t / nt, b = bytes * (t + 1) / nt;
+        memcpy((char*)dst + a, (const char*)src + a, b - a);
+    };
+    for (unsigned t = 1; t < nt; t++) th.emplace_back(work, t);
+    work(0);
+    for (auto& x : th) x.join();
+}
+
+// Places one edge-sized array according to the placement.  Fills *kernel_ptr
+// (what kernels dereference), *owned (what to free) or *borrowed (what to
+// unregister) and adds device bytes to *dev_bytes.
+static emogi_status place_array(int place, bool borrow, int device, const void* src, size_t bytes,
+                                const void** kernel_ptr, void** owned, const void** borrowed,
+                                size_t* dev_bytes, const char* what) {
+    *kernel_ptr = nullptr;
+    *owned = nullptr;
+    *borrowed = nullptr;
+    // pad so that a 16-byte vector access at the last even index stays inside
+    size_t alloc = ((bytes + 127) / 128) * 128 + 128;
+    if (place == EMOGI_PLACE_DEVICE) {
+        void* p = nullptr;
+        EMOGI_TRY(dev_alloc(&p, alloc, what));
+        cudaError_t e = cudaMemcpy(p, src, bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            dev_free(p, alloc);
+            return fail(EMOGI_E_CUDA, "%s: copy to device: %s", what, cudaGetErrorString(e));
+        }
+        *kernel_ptr = p;
+        *owned = p;
+        *dev_bytes += alloc;
+    } else if (place == EMOGI_PLACE_HOST && borrow && bytes == 0) {
+        *kernel_ptr = src;  // nothing to pin; kernels never dereference an empty list
+    } else if (place == EMOGI_PLACE_HOST && borrow) {
+        if (((uintptr_t)src) % 16)
+            return fail(EMOGI_E_ARG, "%s: borrowed arrays must be 16-byte aligned", what);
+        cudaError_t e = cudaHostRegister((void*)src, bytes ? bytes : 16,
+                                         cudaHostRegisterMapped | cudaHostRegisterReadOnly);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            e = cudaHostRegister((void*)src, bytes ? bytes : 16, cudaHostRegisterMapped);
+        }
+        if (e != cudaSuccess) return fail(EMOGI_E_CUDA, "%s: cudaHostRegister: %s", what, cudaGetErrorString(e));
+        void* dp = nullptr;
+        e = cudaHostGetDevicePointer(&dp, (void*)src, 0);
+        if (e != cudaSuccess) {
+            cudaHostUnregister((void*)src);
+            return fail(EMOGI_E_CUDA, "%s: cudaHostGetDevicePointer: %s", what, cudaGetErrorString(e));
+        }
+        *kernel_ptr = dp;
+        *borrowed = src;
+    } else if (place == EMOGI_PLACE_HOST) {
+        void* h = nullptr;
+        cudaError_t e = cudaHostAlloc(&h, alloc, cudaHostAllocMapped);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(EMOGI_E_NOMEM, "%s: cudaHostAlloc(%zu): %s", what, alloc, cudaGetErrorString(e));
+        }
+        parallel_copy(h, src, bytes);
+        memset((char*)h + bytes, 0, alloc - bytes);
+        void* dp = nullptr;
+        e = cudaHostGetDevicePointer(&dp, h, 0);
+        if (e != cudaSuccess) {
+            cudaFreeHost(h);
+            return fail(EMOGI_E_CUDA, "%s: cudaHostGetDevicePointer: %s", what, cudaGetErrorString(e));
+        }
+        *kernel_ptr = dp;
+        *owned = h;
+    } else {  // MANAGED: the UVM baseline, edge list marked read-mostly
+        void* p = nullptr;
+        cudaError_t e = cudaMallocManaged(&p, alloc, cudaMemAttachGlobal);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(EMOGI_E_NOMEM, "%s: cudaMallocManaged(%zu): %s", what, alloc, cudaGetErrorString(e));
+        }
+        parallel_copy(p, src, bytes);
+        memset((char*)p + bytes, 0, alloc - bytes);
+        cudaMemLocation loc;
+        loc.type = cudaMemLocationTypeDevice;
+        loc.id = device;
+        e = cudaMemAdvise(p, alloc, cudaMemAdviseSetReadMostly, loc);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return fail(EMOGI_E_CUDA, "%s: cudaMemAdvise(ReadMostly): %s", what, cudaGetErrorString(e));
+        }
+        *kernel_ptr = p;
+        *owned = p;
+    }
+    return EMOGI_OK;
+}
+
+static void release_array(int place, void* owned, const void* borrowed, size_t bytes) {
+    size_t alloc = ((bytes + 127) / 128) * 128 + 128;
+    if (borrowed) cudaHostUnregister((void*)borrowed);
+    if (!owned) return;
+    if (place == EMOGI_PLACE_DEVICE) dev_free(owned, alloc);
+    else if (place == EMOGI_PLACE_HOST) cudaFreeHost(owned);
+    else cudaFree(owned);
+}
+
+}  // namespace emogi
+
+using namespace emogi;
+
+extern "C" {
+
+const char* emogi_status_string(emogi_status s) {
+    switch (s) {
+        case EMOGI_OK: return "EMOGI_OK";
+        case EMOGI_E_ARG: return "EMOGI_E_ARG";
+        case EMOGI_E_NOMEM: return "EMOGI_E_NOMEM";
+        case EMOGI_E_BUDGET: return "EMOGI_E_BUDGET";
+        case EMOGI_E_CUDA: return "EMOGI_E_CUDA";
+        case EMOGI_E_TIMEOUT: return "EMOGI_E_TIMEOUT";
+        case EMOGI_E_OVERFLOW: return "EMOGI_E_OVERFLOW";
+        case EMOGI_E_UNSUPPORTED: return "EMOGI_E_UNSUPPORTED";
+    }
+    return "EMOGI_E_UNKNOWN";
+}
+
+const char* emogi_last_error(void) { return t_last_error.c_str(); }
+
+const char* emogi_version(void) { return "emogi-gb300 0.1 (sm_103a)"; }
+
+emogi_status emogi_set_device_budget(uint64_t bytes) {
+    g_budget = bytes;
+    return EMOGI_OK;
+}
+
+uint64_t emogi_device_bytes_in_use(void) { return g_in_use.load(); }
+
+void emogi_test_fail_device_alloc_after(int k) { g_fail_after = k > 0 ? k : 0; }
+
+emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets, const uint64_t* col_idx,
+                            const uint32_t* weights, emogi_placement place, uint32_t flags, emogi_graph* out) {
+    clear_error();
+    if (!out) return fail(EMOGI_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (n >= 0xFFFFFFFFull) return fail(EMOGI_E_ARG, "n = %llu must be below 2^32 - 1", (unsigned long long)n);
+    if (!row_offsets) return fail(EMOGI_E_ARG, "row_offsets is NULL");
+    if (m && !col_idx) return fail(EMOGI_E_ARG, "col_idx is NULL");
+    if ((int)place < EMOGI_PLACE_DEVICE || (int)place > EMOGI_PLACE_MANAGED)
+        return fail(EMOGI_E_ARG, "unknown placement %d", (int)place);
+    if (flags & ~(uint32_t)(EMOGI_LOAD_UNDIRECTED | EMOGI_LOAD_BORROW))
+        return fail(EMOGI_E_ARG, "unknown load flags 0x%x", flags);
+    const bool borrow = flags & EMOGI_LOAD_BORROW;
+    if (borrow && place != EMOGI_PLACE_HOST) return fail(EMOGI_E_ARG, "EMOGI_LOAD_BORROW needs EMOGI_PLACE_HOST");
+    EMOGI_TRY(validate_csr(n, m, row_offsets, col_idx));
+
+    emogi_graph g = new (std::nothrow) emogi_graph_s();
+    if (!g) return fail(EMOGI_E_NOMEM, "graph handle");
+    g->n = n;
+    g->m = m;
+    g->flags = flags;
+    g->place = place;
+    g->avg_degree = n ? (double)m / (double)n : 0.0;
+    auto bail = [&](emogi_status s) {
+        emogi_free_graph(g);
+        return s;
+    };
+    if (cudaGetDevice(&g->device) != cudaSuccess) return bail(fail(EMOGI_E_CUDA, "no CUDA device"));
+    cudaError_t e = cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(fail(EMOGI_E_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
+
+    // vertex list in GPU memory (Sec. 4.2)
+    size_t off_bytes = (n + 1) * sizeof(uint64_t);
+    emogi_status s = dev_alloc((void**)&g->d_off, off_bytes, "row offsets");
+    if (s != EMOGI_OK) return bail(s);
+    g->dev_bytes += off_bytes;
+    e = cudaMemcpy(g->d_off, row_offsets, off_bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(fail(EMOGI_E_CUDA, "offsets copy: %s", cudaGetErrorString(e)));
+
+    // edge list (and weights) by placement (Sec. 3.1, Sec. 5.1.2)
+    const void* kp = nullptr;
+    s = place_array(place, borrow, g->device, col_idx, m * sizeof(uint64_t), &kp, &g->cols_owned,
+                    &g->cols_borrowed, &g->dev_bytes, "edge list");
+    if (s != EMOGI_OK) return bail(s);
+    g->cols = (const uint64_t*)kp;
+    g->shift = (uint32_t)(((uintptr_t)g->cols % 128) / 8);
+    if (weights) {
+        if (borrow && ((uintptr_t)weights % 16)) return bail(fail(EMOGI_E_ARG, "borrowed weights must be 16-byte aligned"));
+        s = place_array(place, borrow, g->device, weights, m * sizeof(uint32_t), &kp, &g->w_owned, &g->w_borrowed,
+                        &g->dev_bytes, "weights");
+        if (s != EMOGI_OK) return bail(s);
+        g->w = (const uint32_t*)kp;
+    }
+    *out = g;
+    return EMOGI_OK;
+}
+
+emogi_status emogi_free_graph(emogi_graph g) {
+    if (!g) return EMOGI_OK;
+    cudaSetDevice(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    release_workspace(g);
+    release_array(g->place, g->cols_owned, g->cols_borrowed, g->m * sizeof(uint64_t));
+    if (g->w || g->w_owned || g->w_borrowed) release_array(g->place, g->w_owned, g->w_borrowed, g->m * sizeof(uint32_t));
+    if (g->d_off) dev_free(g->d_off, (g->n + 1) * sizeof(uint64_t));
+    cudaError_t e = cudaSuccess;
+    if (g->stream) e = cudaStreamDestroy(g->stream);
+    delete g;
+    if (e != cudaSuccess) return fail(EMOGI_E_CUDA, "cudaStreamDestroy: %s", cudaGetErrorString(e));
+    return EMOGI_OK;
+}
+
+uint64_t emogi_graph_num_vertices(emogi_graph g) { return g ? g->n : 0; }
+uint64_t emogi_graph_num_edges(emogi_graph g) { return g ? g->m : 0; }
+int emogi_graph_placement(emogi_graph g) { return g ? g->place : -1; }
+
+}  // extern "C"

@@ -1,0 +1,104 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "emogi.h"
+
+namespace emogi {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string& msg);
+void clear_error();
+
+// Records a failure with its message and returns the status.
+emogi_status fail(emogi_status s, const char* fmt, ...);
+
+#define EMOGI_CUDA_TRY(expr)                                                             \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return ::emogi::fail(EMOGI_E_CUDA, "%s failed: %s (%s:%d)", #expr,           \
+                                 cudaGetErrorString(e_), __FILE__, __LINE__);            \
+    } while (0)
+
+#define EMOGI_TRY(expr)                                                                  \
+    do {                                                                                 \
+        emogi_status s_ = (expr);                                                        \
+        if (s_ != EMOGI_OK) return s_;                                                   \
+    } while (0)
+
+// ---------------------------------------------------------------- device memory
+// Every device allocation of the library goes through these so that the
+// budget of emogi_set_device_budget applies and tests can inject failures.
+emogi_status dev_alloc(void** p, size_t bytes, const char* what);
+emogi_status dev_free(void* p, size_t bytes);
+
+// ---------------------------------------------------------------- options
+struct Opts {
+    uint32_t access = EMOGI_ACCESS_MERGED_ALIGNED;
+    uint32_t granularity = 0;
+    uint32_t chunk_lines = 0;
+    uint64_t timeout_ns = 2000000000ull;
+    cudaStream_t stream = nullptr;
+    bool out_on_device = false;
+    uint32_t flags = 0;
+};
+emogi_status parse_opts(const emogi_opts* in, Opts* out);
+
+// ---------------------------------------------------------------- work buffers
+// Device counters of one traversal, kept in one small struct so that a single
+// memset clears them.
+struct DevCounters {
+    uint32_t qcount[2];              // frontier sizes (ping-pong)
+    uint32_t overflow;               // SSSP: a distance reached UINT32_MAX
+    uint32_t error;                  // device-side error code (bounded waits)
+    unsigned long long large[2];     // split-list work: (slots << 34) | items
+    unsigned long long scanned;      // neighbour entries read
+    unsigned long long reached;      // sum of out-degrees of reached vertices
+};
+
+struct Workspace {
+    uint64_t n = 0;
+    uint32_t* q[2] = {nullptr, nullptr};   // frontier queues, n entries each
+    uint32_t* state = nullptr;             // level / dist / parent when output is on the host
+    uint32_t* flag = nullptr;              // SSSP "already queued" flags, all zero between calls
+    uint32_t* lq_v = nullptr;              // split-list vertices
+    unsigned long long* lq_base = nullptr; // first chunk index of each split-list vertex
+    uint64_t lq_cap = 0;
+    DevCounters* ctr = nullptr;
+    DevCounters* h_ctr = nullptr;          // pinned mirror for readback
+    size_t dev_bytes = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+}  // namespace emogi
+
+struct emogi_graph_s {
+    int device = 0;
+    uint64_t n = 0, m = 0;
+    uint32_t flags = 0;
+    int place = EMOGI_PLACE_DEVICE;
+    uint64_t* d_off = nullptr;         // device row offsets (n + 1)
+    const uint64_t* cols = nullptr;    // kernel-visible edge list
+    const uint32_t* w = nullptr;       // kernel-visible weights or null
+    void* cols_owned = nullptr;        // what to free (device / pinned / managed)
+    void* w_owned = nullptr;
+    const void* cols_borrowed = nullptr;  // what to unregister
+    const void* w_borrowed = nullptr;
+    uint32_t shift = 0;                // (edge-list base address mod 128) / 8
+    size_t dev_bytes = 0;              // budgeted device bytes of the graph arrays
+    cudaStream_t stream = nullptr;
+    emogi::Workspace ws;
+    double avg_degree = 0.0;
+};
+
+namespace emogi {
+emogi_status ensure_workspace(emogi_graph g);
+void release_workspace(emogi_graph g);
+int sm_count(int device);
+}  // namespace emogi

@@ -1,0 +1,287 @@
+// Host drivers of BFS, SSSP and CC: the level loop of Sec. 4.2 ("the input
+// graph is traversed by a single vertex depth on every kernel execution") run
+// until no vertex is active (Algorithm "High-level Graph Traversal Flow").
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace emogi {
+namespace {
+
+using dev::Sweep;
+
+constexpr int kThreads = 256;
+constexpr uint32_t kLargeLines = 32;  // lists above 32 lines (4 KiB) are split
+
+struct Ctx {
+    emogi_graph g;
+    Opts o;
+    cudaStream_t st;
+    uint32_t G;
+    uint32_t chunk;
+    int sms;
+    double expand_ms = 0.0;
+    uint64_t expand_launches = 0;
+    uint64_t kernel_launches = 0;
+};
+
+uint32_t auto_granularity(double avg_degree) {
+    if (avg_degree >= 48.0) return 32;
+    if (avg_degree >= 20.0) return 16;
+    if (avg_degree >= 8.0) return 8;
+    return 4;
+}
+
+emogi_status setup(emogi_graph g, const emogi_opts* opts, Ctx* c) {
+    if (!g) return fail(EMOGI_E_ARG, "graph is NULL");
+    EMOGI_TRY(parse_opts(opts, &c->o));
+    c->g = g;
+    EMOGI_CUDA_TRY(cudaSetDevice(g->device));
+    EMOGI_TRY(ensure_workspace(g));
+    c->st = c->o.stream ? c->o.stream : g->stream;
+    c->G = c->o.granularity ? c->o.granularity : auto_granularity(g->avg_degree);
+    c->chunk = c->o.chunk_lines ? c->o.chunk_lines : 32;
+    c->sms = sm_count(g->device);
+    return EMOGI_OK;
+}
+
+int grid_for(const Ctx& c, uint64_t threads_needed) {
+    uint64_t b = (threads_needed + kThreads - 1) / kThreads;
+    uint64_t cap = (uint64_t)c.sms * 8;
+    if (b < 1) b = 1;
+    return (int)std::min(b, cap);
+}
+
+Sweep make_sweep(const Ctx& c, int side, bool all_vertices) {
+    emogi_graph g = c.g;
+    Workspace& ws = g->ws;
+    Sweep s;
+    s.off = g->d_off;
+    s.cols = g->cols;
+    s.w = g->w;
+    s.shift = g->shift;
+    s.in_q = all_vertices ? nullptr : ws.q[side];
+    s.in_count = &ws.ctr->qcount[side];
+    s.all_n = (uint32_t)g->n;
+    s.out_q = ws.q[side ^ 1];
+    s.out_count = &ws.ctr->qcount[side ^ 1];
+    s.lq_v = ws.lq_v;
+    s.lq_base = ws.lq_base;
+    s.large = &ws.ctr->large[0];
+    s.large_lines = kLargeLines;
+    s.chunk_lines = c.chunk;
+    s.scanned = &ws.ctr->scanned;
+    return s;
+}
+
+// One sweep over k active vertices: the neighbour expansion of the chosen
+// access variant (plus the split-list pass for MERGED_ALIGNED).
+template <class Op>
+emogi_status sweep(Ctx& c, const Sweep& s, const Op& op, uint64_t k) {
+    Workspace& ws = c.g->ws;
+    const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
+    if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
+    switch (c.o.access) {
+        case EMOGI_ACCESS_NAIVE:
+            dev::k_expand_naive<Op><<<grid_for(c, k), kThreads, 0, c.st>>>(s, op);
+            c.kernel_launches += 1;
+            break;
+        case EMOGI_ACCESS_MERGED:
+            dev::k_expand_merged<Op><<<grid_for(c, k * 32), kThreads, 0, c.st>>>(s, op);
+            c.kernel_launches += 1;
+            break;
+        default: {
+            const int grid = grid_for(c, k * c.G);
+            switch (c.G) {
+                case 4: dev::k_expand_group<Op, 4><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                case 8: dev::k_expand_group<Op, 8><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                case 16: dev::k_expand_group<Op, 16><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                default: dev::k_expand_group<Op, 32><<<grid, kThreads, 0, c.st>>>(s, op); break;
+            }
+            dev::k_expand_split<Op><<<c.sms * 4, kThreads, 0, c.st>>>(s, op);
+            c.kernel_launches += 2;
+        }
+    }
+    EMOGI_CUDA_TRY(cudaGetLastError());
+    if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[3], c.st));
+    c.expand_launches++;
+    return EMOGI_OK;
+}
+
+emogi_status read_counters(Ctx& c) {
+    Workspace& ws = c.g->ws;
+    EMOGI_CUDA_TRY(cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c.st));
+    EMOGI_CUDA_TRY(cudaStreamSynchronize(c.st));
+    if (c.o.flags & EMOGI_OPT_TIME_KERNELS) {
+        float ms = 0.f;
+        EMOGI_CUDA_TRY(cudaEventElapsedTime(&ms, ws.ev[2], ws.ev[3]));
+        c.expand_ms += ms;
+    }
+    return EMOGI_OK;
+}
+
+// Clears the next-side queue counter and the split-list counter.
+emogi_status reset_sweep_counters(Ctx& c, int side) {
+    Workspace& ws = c.g->ws;
+    EMOGI_CUDA_TRY(cudaMemsetAsync(&ws.ctr->qcount[side ^ 1], 0, sizeof(uint32_t), c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(&ws.ctr->large[0], 0, sizeof(unsigned long long), c.st));
+    return EMOGI_OK;
+}
+
+emogi_status finish(Ctx& c, uint32_t* state, uint32_t* out, bool count_reached, uint32_t iterations,
+                    emogi_stats* stats, bool weights) {
+    emogi_graph g = c.g;
+    Workspace& ws = g->ws;
+    if (count_reached && stats && g->n) {
+        dev::k_reached_edges<<<grid_for(c, g->n), kThreads, 0, c.st>>>(state, g->d_off, (uint32_t)g->n,
+                                                                         &ws.ctr->reached);
+        c.kernel_launches++;
+    }
+    EMOGI_CUDA_TRY(cudaGetLastError());
+    EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[1], c.st));
+    if (!c.o.out_on_device && g->n)
+        EMOGI_CUDA_TRY(cudaMemcpyAsync(out, state, g->n * sizeof(uint32_t), cudaMemcpyDeviceToHost, c.st));
+    EMOGI_CUDA_TRY(cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c.st));
+    EMOGI_CUDA_TRY(cudaStreamSynchronize(c.st));
+    if (stats) {
+        float ms = 0.f;
+        EMOGI_CUDA_TRY(cudaEventElapsedTime(&ms, ws.ev[0], ws.ev[1]));
+        memset(stats, 0, sizeof *stats);
+        stats->iterations = iterations;
+        stats->edges_scanned = ws.h_ctr->scanned;
+        stats->edges_reached = count_reached ? ws.h_ctr->reached : g->m;
+        stats->edge_bytes = ws.h_ctr->scanned * 8ull;
+        stats->weight_bytes = weights ? ws.h_ctr->scanned * 4ull : 0;
+        stats->ms = ms;
+        stats->expand_ms = c.expand_ms;
+        stats->expand_launches = c.expand_launches;
+        stats->kernel_launches = c.kernel_launches;
+    }
+    return EMOGI_OK;
+}
+
+// Level-synchronous loop shared by BFS and SSSP: sweep the active queue until
+// the next queue comes back empty.  make_op(level) builds the sweep's policy.
+template <class MakeOp>
+emogi_status level_loop(Ctx& c, MakeOp make_op, uint32_t* iterations) {
+    int side = 0;
+    uint64_t k = 1;
+    uint32_t it = 0;
+    while (k > 0) {
+        // BFS needs at most n sweeps and frontier Bellman-Ford at most n rounds
+        if (it > c.g->n + 1) return fail(EMOGI_E_TIMEOUT, "traversal did not converge in %u sweeps", it);
+        EMOGI_TRY(reset_sweep_counters(c, side));
+        Sweep s = make_sweep(c, side, false);
+        EMOGI_TRY(sweep(c, s, make_op(it + 1), k));
+        EMOGI_TRY(read_counters(c));
+        k = c.g->ws.h_ctr->qcount[side ^ 1];
+        side ^= 1;
+        it++;
+    }
+    *iterations = it;
+    return EMOGI_OK;
+}
+
+emogi_status check_output(emogi_graph g, const Opts& o, void* out) {
+    if (!out && g->n) return fail(EMOGI_E_ARG, "output pointer is NULL");
+    if (o.out_on_device && out) {
+        cudaPointerAttributes a;
+        if (cudaPointerGetAttributes(&a, out) != cudaSuccess ||
+            (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(EMOGI_E_ARG, "out_on_device is set but the output is not device memory");
+        }
+    }
+    return EMOGI_OK;
+}
+
+}  // namespace
+}  // namespace emogi
+
+using namespace emogi;
+
+extern "C" {
+
+emogi_status emogi_bfs(emogi_graph g, uint64_t src, uint32_t* level, const emogi_opts* opts, emogi_stats* stats) {
+    clear_error();
+    Ctx c;
+    EMOGI_TRY(setup(g, opts, &c));
+    if (src >= g->n) return fail(EMOGI_E_ARG, "source %llu is not below n = %llu", (unsigned long long)src,
+                                 (unsigned long long)g->n);
+    EMOGI_TRY(check_output(g, c.o, level));
+    Workspace& ws = g->ws;
+    uint32_t* state = c.o.out_on_device ? level : ws.state;
+    EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[0], c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ctr, 0, sizeof(DevCounters), c.st));
+    dev::k_init_single<<<grid_for(c, g->n), kThreads, 0, c.st>>>(state, (uint32_t)g->n, (uint32_t)src, ws.q[0],
+                                                                  nullptr, &ws.ctr->qcount[0]);
+    EMOGI_CUDA_TRY(cudaGetLastError());
+    c.kernel_launches++;
+    uint32_t iters = 0;
+    EMOGI_TRY(level_loop(c, [&](uint32_t next) { return dev::BfsOp{state, next}; }, &iters));
+    return finish(c, state, level, true, iters, stats, false);
+}
+
+emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi_opts* opts, emogi_stats* stats) {
+    clear_error();
+    Ctx c;
+    EMOGI_TRY(setup(g, opts, &c));
+    if (src >= g->n) return fail(EMOGI_E_ARG, "source %llu is not below n = %llu", (unsigned long long)src,
+                                 (unsigned long long)g->n);
+    if (!g->w) return fail(EMOGI_E_UNSUPPORTED, "graph was loaded without weights");
+    EMOGI_TRY(check_output(g, c.o, dist));
+    Workspace& ws = g->ws;
+    uint32_t* state = c.o.out_on_device ? dist : ws.state;
+    EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[0], c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ctr, 0, sizeof(DevCounters), c.st));
+    dev::k_init_single<<<grid_for(c, g->n), kThreads, 0, c.st>>>(state, (uint32_t)g->n, (uint32_t)src, ws.q[0],
+                                                                  ws.flag, &ws.ctr->qcount[0]);
+    EMOGI_CUDA_TRY(cudaGetLastError());
+    c.kernel_launches++;
+    uint32_t iters = 0;
+    dev::SsspOp op{state, ws.flag, &ws.ctr->overflow};
+    EMOGI_TRY(level_loop(c, [&](uint32_t) { return op; }, &iters));
+    if (ws.h_ctr->overflow) {
+        // some relaxation overflowed: find out whether a reachable vertex was
+        // left without a distance (its true distance is >= UINT32_MAX)
+        EMOGI_CUDA_TRY(cudaMemsetAsync(&ws.ctr->error, 0, sizeof(uint32_t), c.st));
+        EMOGI_TRY(reset_sweep_counters(c, 0));
+        Sweep s = make_sweep(c, 0, true);
+        EMOGI_TRY(sweep(c, s, dev::OverflowCheckOp{state, &ws.ctr->error}, g->n));
+        EMOGI_TRY(read_counters(c));
+        if (ws.h_ctr->error)
+            return fail(EMOGI_E_OVERFLOW, "a shortest-path distance from %llu does not fit below UINT32_MAX",
+                        (unsigned long long)src);
+    }
+    return finish(c, state, dist, true, iters, stats, true);
+}
+
+emogi_status emogi_cc(emogi_graph g, uint32_t* label, const emogi_opts* opts, emogi_stats* stats) {
+    clear_error();
+    Ctx c;
+    EMOGI_TRY(setup(g, opts, &c));
+    if (!(g->flags & EMOGI_LOAD_UNDIRECTED))
+        return fail(EMOGI_E_UNSUPPORTED, "connected components needs a graph loaded with EMOGI_LOAD_UNDIRECTED");
+    EMOGI_TRY(check_output(g, c.o, label));
+    Workspace& ws = g->ws;
+    uint32_t* parent = c.o.out_on_device ? label : ws.state;
+    EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[0], c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ctr, 0, sizeof(DevCounters), c.st));
+    if (g->n) {
+        dev::k_init_identity<<<grid_for(c, g->n), kThreads, 0, c.st>>>(parent, (uint32_t)g->n);
+        EMOGI_CUDA_TRY(cudaGetLastError());
+        Sweep s = make_sweep(c, 0, true);
+        EMOGI_TRY(sweep(c, s, dev::CcOp{parent}, g->n));
+        dev::k_compress<<<grid_for(c, g->n), kThreads, 0, c.st>>>(parent, (uint32_t)g->n);
+        EMOGI_CUDA_TRY(cudaGetLastError());
+        c.kernel_launches += 2;  // identity init + compress
+        if (c.o.flags & EMOGI_OPT_TIME_KERNELS) EMOGI_TRY(read_counters(c));
+    }
+    return finish(c, parent, label, false, 1, stats, false);
+}
+
+}  // extern "C"

@@ -1,0 +1,265 @@
+"""Thin Python binding of the C ABI in include/emogi.h (ctypes).
+
+Argument marshalling only: every step of a traversal runs in libemogi.so's
+CUDA kernels.  The functions carry the C names without the ``emogi_`` prefix.
+If the shared library has not been built, importing works but the first call
+raises :class:`LibraryNotBuilt` -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libemogi.so")
+
+INF = 0xFFFFFFFF
+MAX_SOURCES = 64
+
+# emogi_status
+OK, E_ARG, E_NOMEM, E_BUDGET, E_CUDA, E_TIMEOUT, E_OVERFLOW, E_UNSUPPORTED = range(8)
+# emogi_placement
+PLACE_DEVICE, PLACE_HOST, PLACE_MANAGED = 0, 1, 2
+PLACEMENTS = {"device": PLACE_DEVICE, "host": PLACE_HOST, "managed": PLACE_MANAGED}
+# load flags
+LOAD_UNDIRECTED, LOAD_BORROW = 1, 2
+# emogi_access
+ACCESS_MERGED_ALIGNED, ACCESS_MERGED, ACCESS_NAIVE = 0, 1, 2
+ACCESS = {"merged_aligned": ACCESS_MERGED_ALIGNED, "aligned": ACCESS_MERGED_ALIGNED,
+          "merged": ACCESS_MERGED, "naive": ACCESS_NAIVE}
+# opts flags
+OPT_TIME_KERNELS = 1
+
+
+class LibraryNotBuilt(RuntimeError):
+    pass
+
+
+class EmogiError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(message)
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("access", ctypes.c_uint32),
+                ("granularity", ctypes.c_uint32), ("chunk_lines", ctypes.c_uint32),
+                ("timeout_ns", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
+                ("out_on_device", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("edges_scanned", ctypes.c_uint64), ("edges_reached", ctypes.c_uint64),
+                ("edge_bytes", ctypes.c_uint64), ("weight_bytes", ctypes.c_uint64),
+                ("ms", ctypes.c_double), ("expand_ms", ctypes.c_double),
+                ("expand_launches", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+# (name, restype, argtypes) of every exported entry point
+_P, _U64, _U32, _I32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+_SIGNATURES = [
+    ("emogi_load_csr", _I32, [_U64, _U64, _P, _P, _P, _I32, _U32, ctypes.POINTER(_P)]),
+    ("emogi_bfs", _I32, [_P, _U64, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+    ("emogi_sssp", _I32, [_P, _U64, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+    ("emogi_cc", _I32, [_P, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+    ("emogi_set_device_budget", _I32, [_U64]),
+    ("emogi_device_bytes_in_use", _U64, []),
+    ("emogi_free_graph", _I32, [_P]),
+    ("emogi_graph_num_vertices", _U64, [_P]),
+    ("emogi_graph_num_edges", _U64, [_P]),
+    ("emogi_graph_placement", _I32, [_P]),
+    ("emogi_status_string", ctypes.c_char_p, [_I32]),
+    ("emogi_last_error", ctypes.c_char_p, []),
+    ("emogi_version", ctypes.c_char_p, []),
+    ("emogi_test_fail_device_alloc_after", None, [_I32]),
+]
+
+_lib_handle = None
+
+
+def lib():
+    """The loaded libemogi.so (raises LibraryNotBuilt if it is missing)."""
+    global _lib_handle
+    if _lib_handle is None:
+        if not os.path.exists(LIB_PATH):
+            raise LibraryNotBuilt(
+                f"{LIB_PATH} is missing: build the CUDA library first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGNATURES:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib_handle = L
+    return _lib_handle
+
+
+def exported_names():
+    return [s[0] for s in _SIGNATURES]
+
+
+def _check(status: int):
+    if status != OK:
+        msg = lib().emogi_last_error().decode(errors="replace")
+        raise EmogiError(status, msg or status_string(status))
+
+
+def status_string(status: int) -> str:
+    return lib().emogi_status_string(status).decode()
+
+
+def last_error() -> str:
+    return lib().emogi_last_error().decode(errors="replace")
+
+
+def version() -> str:
+    return lib().emogi_version().decode()
+
+
+def set_device_budget(nbytes: int):
+    _check(lib().emogi_set_device_budget(int(nbytes)))
+
+
+def device_bytes_in_use() -> int:
+    return int(lib().emogi_device_bytes_in_use())
+
+
+def test_fail_device_alloc_after(k: int):
+    lib().emogi_test_fail_device_alloc_after(int(k))
+
+
+def _host_array(a, dtype, name):
+    if a is None:
+        return None
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr
+
+
+class Graph:
+    """A loaded CSR graph (owns the C handle; call free() or use `with`)."""
+
+    def __init__(self, handle, n, m, placement, keepalive=()):
+        self._h = ctypes.c_void_p(handle)
+        self.n = n
+        self.m = m
+        self.placement = placement
+        self._keepalive = keepalive  # borrowed host arrays stay alive with the handle
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise EmogiError(E_ARG, "graph already freed")
+        return self._h
+
+    def free(self):
+        if self._h:
+            h, self._h = self._h, ctypes.c_void_p(None)
+            _check(lib().emogi_free_graph(h))
+            self._keepalive = ()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().emogi_free_graph(self._h)
+        except Exception:
+            pass
+
+
+def load_csr(n, m, row_offsets, col_idx, weights=None, placement="host", flags=0,
+             undirected: Optional[bool] = None, borrow: bool = False) -> Graph:
+    """emogi_load_csr: copy (or, with borrow, pin in place) a CSR graph."""
+    place = PLACEMENTS[placement] if isinstance(placement, str) else int(placement)
+    f = int(flags)
+    if undirected:
+        f |= LOAD_UNDIRECTED
+    if borrow:
+        f |= LOAD_BORROW
+    off = _host_array(row_offsets, np.uint64, "row_offsets")
+    col = _host_array(col_idx, np.uint64, "col_idx")
+    w = _host_array(weights, np.uint32, "weights")
+    h = ctypes.c_void_p()
+    st = lib().emogi_load_csr(int(n), int(m), off.ctypes.data,
+                              col.ctypes.data if col is not None else None,
+                              w.ctypes.data if w is not None else None,
+                              place, f, ctypes.byref(h))
+    _check(st)
+    keep = (col, w) if (f & LOAD_BORROW) else ()
+    return Graph(h.value, int(n), int(m), place, keep)
+
+
+def load_graph(g, placement="host", borrow=False, with_weights=True) -> Graph:
+    """Load a graphgen.Graph-like object (n, offsets, cols, weights, undirected)."""
+    w = g.weights if with_weights else None
+    return load_csr(g.n, g.m, g.offsets, g.cols, w, placement=placement,
+                    undirected=bool(getattr(g, "undirected", False)), borrow=borrow)
+
+
+def _opts(access=None, granularity=0, chunk_lines=0, timeout_ns=0, stream=None, out_on_device=False,
+          time_kernels=False):
+    o = Opts()
+    o.struct_size = ctypes.sizeof(Opts)
+    o.access = ACCESS[access] if isinstance(access, str) else int(access or 0)
+    o.granularity = int(granularity)
+    o.chunk_lines = int(chunk_lines)
+    o.timeout_ns = int(timeout_ns)
+    if stream is not None:
+        o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
+    o.out_on_device = 1 if out_on_device else 0
+    o.flags = OPT_TIME_KERNELS if time_kernels else 0
+    return o
+
+
+def _out_buffer(n, out):
+    """Returns (pointer, result object, on_device)."""
+    if out is None:
+        arr = np.empty(max(n, 1), dtype=np.uint32)
+        return arr.ctypes.data, arr[:n], False
+    if hasattr(out, "data_ptr"):  # torch tensor
+        if out.numel() < n or out.element_size() != 4 or not out.is_contiguous():
+            raise EmogiError(E_ARG, "output tensor must be contiguous, 4-byte and hold n entries")
+        return out.data_ptr(), out, bool(out.is_cuda)
+    arr = out
+    if arr.dtype != np.uint32 or arr.size < n or not arr.flags.c_contiguous:
+        raise EmogiError(E_ARG, "output array must be contiguous uint32 with n entries")
+    return arr.ctypes.data, arr, False
+
+
+def _run(fn, g: Graph, args, out, kw):
+    ptr, res, on_dev = _out_buffer(g.n, out)
+    o = _opts(out_on_device=on_dev, **kw)
+    s = Stats()
+    _check(fn(g.handle, *args, ptr, ctypes.byref(o), ctypes.byref(s)))
+    return res, s.as_dict()
+
+
+def bfs(g: Graph, src: int, out=None, **kw):
+    """emogi_bfs -> (level array, stats dict)."""
+    return _run(lib().emogi_bfs, g, (int(src),), out, kw)
+
+
+def sssp(g: Graph, src: int, out=None, **kw):
+    """emogi_sssp -> (dist array, stats dict)."""
+    return _run(lib().emogi_sssp, g, (int(src),), out, kw)
+
+
+def cc(g: Graph, out=None, **kw):
+    """emogi_cc -> (label array, stats dict)."""
+    return _run(lib().emogi_cc, g, (), out, kw)
+
+
+def free_graph(g: Graph):
+    g.free()

@@ -1,0 +1,270 @@
+"""GPU parity: every CUDA result equals the CPU oracle element by element.
+
+All traversal results are integers, so the bar is bit-exact.  Covered: every
+access variant (naive / merged / merged+aligned at each granularity) and every
+placement (device / pinned host / managed), borrowed host arrays, device
+outputs, the split path for long lists, lists starting at every residue of the
+128-byte line, empty / ragged / degenerate graphs, the SSSP overflow check and
+host-side error paths.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2006_06890_gb300 import emogi as E  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2006_06890_gb300 import _build
+    _build.build()
+    E.lib()
+    yield
+
+
+# ------------------------------------------------------------------ graphs
+def residue_graph():
+    """Rows of length 0..40 so list starts fall on every index mod 16."""
+    rng = np.random.default_rng(1)
+    n = 400
+    s, d = [], []
+    for v in range(n):
+        deg = v % 41
+        for u in rng.integers(0, n, size=deg):
+            s.append(v)
+            d.append(int(u))
+    return gg.csr_from_edges(n, s, d, weights=rng.integers(1, 256, size=len(s)), symmetrize=False,
+                             dedup=False, drop_self_loops=False, sort=False, name="residues")
+
+
+def hub_graph(n=200_000):
+    """A star whose centre has n-1 neighbours (the split path) plus a ring."""
+    c = np.zeros(n - 1, dtype=np.uint64)
+    leaves = np.arange(1, n, dtype=np.uint64)
+    ring_s = np.arange(1, n, dtype=np.uint64)
+    ring_d = np.concatenate([np.arange(2, n), [1]]).astype(np.uint64)
+    g = gg.csr_from_edges(n, np.concatenate([c, ring_s]), np.concatenate([leaves, ring_d]), name="hub")
+    return gg.add_weights(g, seed=3)
+
+
+def directed_multigraph():
+    rng = np.random.default_rng(7)
+    n, m = 3000, 20000
+    s = rng.integers(0, n, size=m)
+    d = rng.integers(0, n, size=m)
+    w = rng.integers(1, 256, size=m)
+    g = gg.csr_from_edges(n, s, d, weights=w, symmetrize=False, dedup=False, drop_self_loops=False,
+                          sort=False, name="directed-multi")
+    g.undirected = False
+    return g
+
+
+GRAPHS = {}
+
+
+def graph(name):
+    if name not in GRAPHS:
+        if name == "kron16":  # the 65,536-vertex Kronecker workload (edge factor 16)
+            GRAPHS[name] = gg.kronecker(16, 16, seed=1, weights=True)
+        elif name == "kron12":
+            GRAPHS[name] = gg.kronecker(12, 16, seed=3, weights=True)
+        elif name == "urand14":
+            GRAPHS[name] = gg.uniform(1 << 14, 7, seed=2, weights=True)
+        elif name == "path":
+            GRAPHS[name] = gg.add_weights(gg.path_graph(3000), seed=1)
+        elif name == "residues":
+            GRAPHS[name] = residue_graph()
+        elif name == "hub":
+            GRAPHS[name] = hub_graph()
+        elif name == "directed":
+            GRAPHS[name] = directed_multigraph()
+        elif name == "empty":
+            GRAPHS[name] = gg.add_weights(gg.empty_graph(7), seed=1)
+        elif name == "single":
+            GRAPHS[name] = gg.add_weights(gg.empty_graph(1), seed=1)
+        else:
+            raise KeyError(name)
+    return GRAPHS[name]
+
+
+def sources(g, k=2):
+    out = [gg.max_degree_vertex(g)]
+    out += [int(x) for x in gg.random_sources(g, k, seed=2)]
+    out.append(int(np.argmin(g.degrees())))  # possibly an isolated vertex
+    return sorted(set(out))
+
+
+def check_all(g, h, **kw):
+    for s in sources(g):
+        lv, st = E.bfs(h, s, **kw)
+        exp = oracle.bfs_g(g, s)
+        np.testing.assert_array_equal(lv, exp, err_msg=f"bfs src={s} {kw}")
+        assert st["edges_reached"] == oracle.reached_edges(g.offsets, exp)
+        if g.weights is not None:
+            d, _ = E.sssp(h, s, **kw)
+            np.testing.assert_array_equal(d, oracle.sssp_g(g, s), err_msg=f"sssp src={s} {kw}")
+    if g.undirected:
+        lab, st = E.cc(h, **kw)
+        np.testing.assert_array_equal(lab, oracle.cc_g(g), err_msg=f"cc {kw}")
+        assert st["edges_scanned"] == g.m
+
+
+VARIANTS = [dict(access="merged_aligned"), dict(access="merged_aligned", granularity=4),
+            dict(access="merged_aligned", granularity=8), dict(access="merged_aligned", granularity=16),
+            dict(access="merged_aligned", granularity=32), dict(access="merged"), dict(access="naive")]
+VID = ["aligned-auto", "aligned-g4", "aligned-g8", "aligned-g16", "aligned-g32", "merged", "naive"]
+
+
+# ------------------------------------------------------------------ parity
+@pytest.mark.parametrize("placement", ["device", "host", "managed"])
+@pytest.mark.parametrize("variant", VARIANTS, ids=VID)
+def test_kron16_all_variants_and_placements(placement, variant):
+    g = graph("kron16")
+    with E.load_graph(g, placement=placement) as h:
+        check_all(g, h, **variant)
+
+
+@pytest.mark.parametrize("name", ["kron12", "urand14", "path", "residues", "hub", "directed", "empty", "single"])
+@pytest.mark.parametrize("variant", VARIANTS, ids=VID)
+def test_graph_set_host(name, variant):
+    g = graph(name)
+    with E.load_graph(g, placement="host") as h:
+        check_all(g, h, **variant)
+
+
+@pytest.mark.parametrize("chunk", [1, 3, 32, 500])
+def test_split_chunk_sizes(chunk):
+    g = graph("hub")
+    with E.load_graph(g, placement="device") as h:
+        check_all(g, h, access="merged_aligned", granularity=8, chunk_lines=chunk)
+
+
+def test_borrowed_host_arrays_at_every_line_offset():
+    """EMOGI_LOAD_BORROW pins the caller's arrays in place; bases that are not
+    128-byte aligned (but 16-byte aligned) still give exact results."""
+    g = graph("residues")
+    for shift_elems in (0, 2, 4, 6, 8, 10, 12, 14):
+        cols = gg.aligned_empty(g.m + 16, np.uint64, 128)[shift_elems:shift_elems + g.m]
+        cols[:] = g.cols
+        w_off = 2 * shift_elems  # 0, 4, ..., 28 weights: 16-byte aligned, every 16-byte slot of a line
+        w = gg.aligned_empty(g.m + 32, np.uint32, 128)[w_off:w_off + g.m]
+        w[:] = g.weights
+        assert cols.ctypes.data % 16 == 0 and w.ctypes.data % 16 == 0
+        with E.load_csr(g.n, g.m, g.offsets, cols, w, placement="host", borrow=True,
+                        undirected=False) as h:
+            check_all(g, h)
+
+
+def test_device_outputs_with_torch_tensors():
+    g = graph("kron12")
+    s = gg.max_degree_vertex(g)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.Stream()
+    with E.load_graph(g, placement="host") as h:
+        E.bfs(h, s, out=out, stream=stream)
+        np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), oracle.bfs_g(g, s))
+        E.sssp(h, s, out=out)
+        np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), oracle.sssp_g(g, s))
+        E.cc(h, out=out)
+        np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), oracle.cc_g(g))
+
+
+def test_repeated_calls_reuse_buffers():
+    g = graph("urand14")
+    srcs = sources(g, 4)
+    with E.load_graph(g, placement="host") as h:
+        for _ in range(2):
+            for s in srcs:
+                np.testing.assert_array_equal(E.sssp(h, s)[0], oracle.sssp_g(g, s))
+                np.testing.assert_array_equal(E.bfs(h, s)[0], oracle.bfs_g(g, s))
+
+
+def test_unit_weights_sssp_equals_bfs():
+    g = gg.kronecker(11, 16, seed=8)
+    g.weights = np.ones(g.m, dtype=np.uint32)
+    s = gg.max_degree_vertex(g)
+    with E.load_graph(g, placement="host") as h:
+        np.testing.assert_array_equal(E.sssp(h, s)[0], E.bfs(h, s)[0])
+
+
+def test_sssp_overflow_is_reported():
+    g = gg.csr_from_edges(4, [0, 1, 2], [1, 2, 3], weights=[0x7FFFFFFF, 0x7FFFFFFF, 5],
+                          symmetrize=False)
+    with E.load_graph(g, placement="device") as h:
+        with pytest.raises(E.EmogiError) as ei:
+            E.sssp(h, 0)
+        assert ei.value.status == E.E_OVERFLOW
+        # a large but representable distance is not an overflow
+        d, _ = E.sssp(h, 1)
+        assert d.tolist() == [E.INF, 0, 0x7FFFFFFF, 0x7FFFFFFF + 5]
+
+
+def test_sssp_spurious_overflow_candidate_is_cleared():
+    """A relaxation can overflow from a non-final distance while every true
+    distance fits: the long detour 0->1->2 is relaxed before the short edge
+    0->2 lowers dist[2]; the result must be exact and not an error."""
+    big = 0xFFFFFF00
+    g = gg.csr_from_edges(4, [0, 0, 1, 2], [1, 2, 2, 3], weights=[big, 3, 1000, 7], symmetrize=False)
+    with E.load_graph(g, placement="device") as h:
+        d, _ = E.sssp(h, 0, access="naive")
+        np.testing.assert_array_equal(d, oracle.sssp_g(g, 0))
+
+
+def test_errors():
+    g = graph("directed")
+    with E.load_graph(g, placement="host") as h:
+        with pytest.raises(E.EmogiError) as ei:
+            E.bfs(h, g.n)
+        assert ei.value.status == E.E_ARG
+        with pytest.raises(E.EmogiError) as ei:
+            E.cc(h)
+        assert ei.value.status == E.E_UNSUPPORTED
+    with E.load_graph(g, placement="host", with_weights=False) as h:
+        with pytest.raises(E.EmogiError) as ei:
+            E.sssp(h, 0)
+        assert ei.value.status == E.E_UNSUPPORTED
+
+
+def test_budget_and_injected_alloc_failure():
+    g = graph("kron12")
+    base = E.device_bytes_in_use()
+    E.set_device_budget(base + 1024)
+    try:
+        with pytest.raises(E.EmogiError) as ei:
+            E.load_graph(g, placement="device")
+        assert ei.value.status == E.E_BUDGET
+    finally:
+        E.set_device_budget(0)
+    assert E.device_bytes_in_use() == base
+    E.test_fail_device_alloc_after(2)
+    try:
+        with pytest.raises(E.EmogiError) as ei:
+            E.load_graph(g, placement="device")
+        assert ei.value.status == E.E_NOMEM
+    finally:
+        E.test_fail_device_alloc_after(0)
+    assert E.device_bytes_in_use() == base
+    with E.load_graph(g, placement="host") as h:  # allocations work again
+        np.testing.assert_array_equal(E.cc(h)[0], oracle.cc_g(g))
+    assert E.device_bytes_in_use() == base
+
+
+def test_stats_are_consistent():
+    g = graph("kron16")
+    s = gg.max_degree_vertex(g)
+    with E.load_graph(g, placement="host") as h:
+        lv, st = E.bfs(h, s, time_kernels=True)
+        reached = oracle.reached_edges(g.offsets, lv)
+        assert st["edges_scanned"] == reached  # BFS expands each reached vertex once
+        assert st["edge_bytes"] == 8 * reached
+        assert st["iterations"] == int(lv[lv != E.INF].max()) + 1
+        assert st["expand_launches"] == st["iterations"]
+        assert 0 < st["expand_ms"] <= st["ms"]
