@@ -346,11 +346,19 @@ def oracle_step(g, src):
 
 
 def cpu_baseline(g, src):
-    edges, ts = oracle_step(g, src)
-    tot = sum(ts)
+    """The oracle's BFS and CC on the full graph (Dijkstra alone takes over a
+    minute on one core, so it is left out of this bounded sample)."""
+    import oracle
+    t0 = time.perf_counter()
+    lv = oracle.bfs_g(g, src)
+    t1 = time.perf_counter()
+    oracle.cc_g(g)
+    t2 = time.perf_counter()
+    edges = oracle.reached_edges(g.offsets, lv) + g.m
+    tot = t2 - t0
     return {"value": round(edges / tot / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"one step (BFS + Dijkstra from vertex {src} + union-find CC) on the full graph, "
-                      f"single-threaded C; {tot:.1f} s (bfs {ts[0]:.1f}, sssp {ts[1]:.1f}, cc {ts[2]:.1f})"}
+            "sample": f"BFS from vertex {src} + union-find CC on the full graph, single-threaded C; "
+                      f"{tot:.1f} s (bfs {t1 - t0:.1f}, cc {t2 - t1:.1f})"}
 
 
 # ------------------------------------------------------------------ reference arm

@@ -92,6 +92,10 @@ typedef struct {
     void* cuda_stream;     /* cudaStream_t to run on; NULL = the graph's own stream */
     int32_t out_on_device; /* 1: output pointers are device pointers of the current device */
     uint32_t flags;        /* EMOGI_OPT_* */
+    uint32_t delta;        /* SSSP bucket width: vertices are expanded in order of distance
+                              windows [T - delta, T); 0 = automatic, UINT32_MAX = plain
+                              frontier Bellman-Ford (one window) */
+    uint32_t reserved0;
 } emogi_opts;
 
 /* Per-call statistics (optional output). */
@@ -140,9 +144,11 @@ emogi_status emogi_bfs(emogi_graph g, uint64_t src, uint32_t* level, const emogi
                        emogi_stats* stats);
 
 /* Single-source shortest paths with the graph's uint32 weights (Sec. 5.1.2,
- * Sec. 5.4: SSSP reads each weight beside its edge).  Frontier-based
- * Bellman-Ford: active vertices relax their out-edges with an atomic minimum
- * and improved vertices become active, until no distance changes.
+ * Sec. 5.4: SSSP reads each weight beside its edge).  Active vertices relax
+ * their out-edges with an atomic minimum and improved vertices become active,
+ * until no distance changes; active vertices are expanded in distance windows
+ * of width opts->delta (a near frontier below the threshold, a far pile above
+ * it), which bounds re-expansions without changing the exact result.
  *   dist   uint32_t[n] output: exact shortest distance, EMOGI_INF if unreachable.
  * Errors: as emogi_bfs, plus EMOGI_E_UNSUPPORTED (graph loaded without
  * weights) and EMOGI_E_OVERFLOW (a finite distance >= UINT32_MAX). */

@@ -101,6 +101,7 @@ emogi_status parse_opts(const emogi_opts* in, Opts* o) {
     o->access = in->access;
     o->granularity = in->granularity;
     o->chunk_lines = in->chunk_lines;
+    if (in->struct_size >= offsetof(emogi_opts, delta) + sizeof(uint32_t)) o->delta = in->delta;
     if (in->timeout_ns) o->timeout_ns = in->timeout_ns;
     o->stream = (cudaStream_t)in->cuda_stream;
     o->out_on_device = in->out_on_device != 0;
@@ -123,7 +124,11 @@ emogi_status ensure_workspace(emogi_graph g) {
         {(void**)&ws.q[0], n * 4, "frontier queue 0"},
         {(void**)&ws.q[1], n * 4, "frontier queue 1"},
         {(void**)&ws.state, n * 4, "vertex state"},
-        {(void**)&ws.flag, n * 4, "queued flags"},
+        {(void**)&ws.flag, n * 4, "near flags"},
+        {(void**)&ws.fflag, n * 4, "far flags"},
+        {(void**)&ws.fq[0], n * 4, "far pile 0"},
+        {(void**)&ws.fq[1], n * 4, "far pile 1"},
+        {(void**)&ws.xd, n * 4, "expanded distances"},
         {(void**)&ws.lq_v, ws.lq_cap * 4, "split-list vertices"},
         {(void**)&ws.lq_base, ws.lq_cap * 8, "split-list chunk bases"},
         {(void**)&ws.ctr, sizeof(DevCounters), "counters"},
@@ -138,6 +143,7 @@ emogi_status ensure_workspace(emogi_graph g) {
     }
     cudaError_t e = cudaHostAlloc((void**)&ws.h_ctr, sizeof(DevCounters), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMemset(ws.flag, 0, n * 4);
+    if (e == cudaSuccess) e = cudaMemset(ws.fflag, 0, n * 4);
     for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&ws.ev[i]);
     if (e != cudaSuccess) {
         release_workspace(g);
@@ -152,6 +158,10 @@ void release_workspace(emogi_graph g) {
     dev_free(ws.q[1], ws.n * 4);
     dev_free(ws.state, ws.n * 4);
     dev_free(ws.flag, ws.n * 4);
+    dev_free(ws.fflag, ws.n * 4);
+    dev_free(ws.fq[0], ws.n * 4);
+    dev_free(ws.fq[1], ws.n * 4);
+    dev_free(ws.xd, ws.n * 4);
     dev_free(ws.lq_v, ws.lq_cap * 4);
     dev_free(ws.lq_base, ws.lq_cap * 8);
     dev_free(ws.ctr, sizeof(DevCounters));
@@ -378,6 +388,12 @@ emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets,
     g->cols = (const uint64_t*)kp;
     g->shift = (uint32_t)(((uintptr_t)g->cols % 128) / 8);
     if (weights) {
+        // mean weight from up to 2^20 evenly spaced entries
+        const uint64_t stride = m > (1u << 20) ? m / (1u << 20) : 1;
+        double sum = 0.0;
+        uint64_t cnt = 0;
+        for (uint64_t i = 0; i < m; i += stride, cnt++) sum += weights[i];
+        g->avg_weight = cnt ? sum / (double)cnt : 0.0;
         if (borrow && ((uintptr_t)weights % 16)) return bail(fail(EMOGI_E_ARG, "borrowed weights must be 16-byte aligned"));
         s = place_array(place, borrow, g->device, weights, m * sizeof(uint32_t), &kp, &g->w_owned, &g->w_borrowed,
                         &g->dev_bytes, "weights");

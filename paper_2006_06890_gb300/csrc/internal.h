@@ -43,6 +43,7 @@ struct Opts {
     uint32_t access = EMOGI_ACCESS_MERGED_ALIGNED;
     uint32_t granularity = 0;
     uint32_t chunk_lines = 0;
+    uint32_t delta = 0;
     uint64_t timeout_ns = 2000000000ull;
     cudaStream_t stream = nullptr;
     bool out_on_device = false;
@@ -55,8 +56,11 @@ emogi_status parse_opts(const emogi_opts* in, Opts* out);
 // memset clears them.
 struct DevCounters {
     uint32_t qcount[2];              // frontier sizes (ping-pong)
+    uint32_t fcount[2];              // SSSP far-pile sizes (ping-pong)
+    uint32_t far_min;                // SSSP: smallest distance sent to the far pile
     uint32_t overflow;               // SSSP: a distance reached UINT32_MAX
     uint32_t error;                  // device-side error code (bounded waits)
+    uint32_t pad;
     unsigned long long large[2];     // split-list work: (slots << 34) | items
     unsigned long long scanned;      // neighbour entries read
     unsigned long long reached;      // sum of out-degrees of reached vertices
@@ -66,7 +70,11 @@ struct Workspace {
     uint64_t n = 0;
     uint32_t* q[2] = {nullptr, nullptr};   // frontier queues, n entries each
     uint32_t* state = nullptr;             // level / dist / parent when output is on the host
-    uint32_t* flag = nullptr;              // SSSP "already queued" flags, all zero between calls
+    uint32_t* flag = nullptr;              // SSSP "in near frontier" flags, all zero between calls
+    uint32_t* fflag = nullptr;             // SSSP "in far pile" flags, all zero between calls
+    uint32_t* fq[2] = {nullptr, nullptr};  // SSSP far piles
+    uint32_t* xd = nullptr;                // SSSP distance of the last expansion
+    bool flags_dirty = false;              // a call ended early and left flags set
     uint32_t* lq_v = nullptr;              // split-list vertices
     unsigned long long* lq_base = nullptr; // first chunk index of each split-list vertex
     uint64_t lq_cap = 0;
@@ -95,6 +103,7 @@ struct emogi_graph_s {
     cudaStream_t stream = nullptr;
     emogi::Workspace ws;
     double avg_degree = 0.0;
+    double avg_weight = 0.0;           // mean of a sample of the weights
 };
 
 namespace emogi {

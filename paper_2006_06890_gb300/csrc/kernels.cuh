@@ -118,6 +118,16 @@ __device__ __forceinline__ void defer(const Sweep& c, uint32_t v, unsigned long 
 }
 
 // ------------------------------------------------------------------ applications
+// The per-neighbour work of a sweep is a policy object.  Each thread works on
+// its own copy, so a policy may keep per-thread accumulators.
+//   begin(v)       one lane per active vertex, before the list is read: returns
+//                  the 32-bit value broadcast to the lanes reading v's list, or
+//                  INF to skip the list entirely;
+//   begin_chunk(v) the same for one work item of a split (long) list;
+//   visit(st,v,u,w) the update for edge (v, u) with weight w; true = push u to
+//                  the next frontier;
+//   flush()        once per thread at kernel end, whole warp converged.
+
 // BFS (Sec. 2.1): an unvisited neighbour gets the next level and becomes active.
 // The compare-and-swap makes exactly one visitor push it.
 struct BfsOp {
@@ -125,48 +135,77 @@ struct BfsOp {
     uint32_t next;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = true;
-    __device__ __forceinline__ void pre(uint32_t) const {}
-    __device__ __forceinline__ uint32_t begin(uint32_t, bool) const { return 0; }
-    __device__ __forceinline__ bool visit(uint32_t, uint32_t, uint64_t u, uint32_t) const {
+    __device__ __forceinline__ uint32_t begin(uint32_t) { return 0; }
+    __device__ __forceinline__ uint32_t begin_chunk(uint32_t) { return 0; }
+    __device__ __forceinline__ bool visit(uint32_t, uint32_t, uint64_t u, uint32_t) {
         uint32_t* p = level + (uint32_t)u;
         if (*p != INF) return false;
         return atomicCAS(p, INF, next) == INF;
     }
+    __device__ __forceinline__ void flush() {}
 };
 
-// SSSP (Sec. 5.1.2): relax dist[u] with dist[v] + w by an atomic minimum; an
-// improved neighbour becomes active unless it is already queued.  `flag`
-// records "queued for the next round"; a vertex clears its flag before it
-// reads its own distance, so an improvement that lands after the read always
-// queues the vertex again.
+// Warp-reduced atomic minimum of a per-thread value (whole warp converged).
+__device__ __forceinline__ void warp_atomic_min(uint32_t* out, uint32_t x) {
+    x = __reduce_min_sync(0xffffffffu, x);
+    if ((threadIdx.x & 31) == 0 && x != INF) atomicMin(out, x);
+}
+
+// SSSP (Sec. 5.1.2, Sec. 5.4: weights are read beside the edges).  Relaxation
+// by atomic minimum with a near/far split of the active set (delta-stepping
+// order): an improved neighbour whose new distance is below the threshold T
+// joins the next near frontier, otherwise the far pile.  When the near
+// frontier empties, the far pile is split again with T raised past its
+// smallest distance.  Every vertex is expanded with its final distance, so
+// the fixed point is the exact shortest distance whatever the order.
+//   nflag / fflag: "queued in the near frontier / far pile" (one entry each);
+//   xd: the distance v was last expanded with, so a vertex queued twice
+//   (near and far) is not expanded twice with the same distance.
+// A vertex clears its near flag before it reads its distance, so an
+// improvement landing after the read queues it again.
 struct SsspOp {
     uint32_t* dist;
-    uint32_t* flag;
+    uint32_t* nflag;
+    uint32_t* fflag;
+    uint32_t* xd;
+    uint32_t* far_q;
+    uint32_t* far_count;
+    uint32_t* far_min;
     uint32_t* overflow;
+    uint32_t T;
+    uint32_t lmin;  // per-thread smallest distance sent to the far pile
     static constexpr bool kWeights = true;
     static constexpr bool kPush = true;
-    __device__ __forceinline__ void pre(uint32_t v) const {
-        atomicExch(flag + v, 0u);
+    __device__ __forceinline__ uint32_t begin(uint32_t v) {
+        atomicExch(nflag + v, 0u);
         __threadfence();
+        const uint32_t d = __ldcg(dist + v);
+        if (d >= __ldcg(xd + v)) return INF;  // already expanded with this distance
+        __stcg(xd + v, d);
+        return d;
     }
-    __device__ __forceinline__ uint32_t begin(uint32_t v, bool active) const {
-        return active ? __ldcg(dist + v) : INF;
-    }
+    __device__ __forceinline__ uint32_t begin_chunk(uint32_t v) { return __ldcg(dist + v); }
     // A relaxation whose sum does not fit below INF is dropped and noted; the
     // host then checks whether some reachable vertex was left at INF.
-    __device__ __forceinline__ bool visit(uint32_t dv, uint32_t, uint64_t u, uint32_t w) const {
-        const uint64_t nd = (uint64_t)dv + (uint64_t)w;
-        if (nd >= (uint64_t)INF) {
+    __device__ __forceinline__ bool visit(uint32_t dv, uint32_t, uint64_t u64, uint32_t w) {
+        const uint32_t u = (uint32_t)u64;
+        const uint64_t nd64 = (uint64_t)dv + (uint64_t)w;
+        if (nd64 >= (uint64_t)INF) {
             if (dv != INF) atomicExch(overflow, 1u);
             return false;
         }
-        uint32_t* p = dist + (uint32_t)u;
-        if ((uint32_t)nd >= *p) return false;
-        const uint32_t old = atomicMin(p, (uint32_t)nd);
-        if ((uint32_t)nd >= old) return false;
+        const uint32_t nd = (uint32_t)nd64;
+        uint32_t* p = dist + u;
+        if (nd >= *p) return false;
+        const uint32_t old = atomicMin(p, nd);
+        if (nd >= old) return false;
         __threadfence();
-        return atomicExch(flag + (uint32_t)u, 1u) == 0u;
+        if (nd < T) return atomicExch(nflag + u, 1u) == 0u;
+        lmin = nd < lmin ? nd : lmin;
+        if (atomicExch(fflag + u, 1u) == 0u) push(far_q, far_count, u);
+        return false;
     }
+    __device__ __forceinline__ void flush() { warp_atomic_min(far_min, lmin); }
 };
 
 // Union-find root with path halving.  Parents only ever point to smaller ids
@@ -190,9 +229,9 @@ struct CcOp {
     uint32_t* parent;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = false;
-    __device__ __forceinline__ void pre(uint32_t) const {}
-    __device__ __forceinline__ uint32_t begin(uint32_t, bool) const { return 0; }
-    __device__ __forceinline__ bool visit(uint32_t, uint32_t v, uint64_t u64, uint32_t) const {
+    __device__ __forceinline__ uint32_t begin(uint32_t) { return 0; }
+    __device__ __forceinline__ uint32_t begin_chunk(uint32_t) { return 0; }
+    __device__ __forceinline__ bool visit(uint32_t, uint32_t v, uint64_t u64, uint32_t) {
         uint32_t u = (uint32_t)u64;
         if (u >= v) return false;
         uint32_t a = v, b = u;
@@ -204,6 +243,7 @@ struct CcOp {
             if (atomicCAS(parent + hi, hi, lo) == hi) return false;
         }
     }
+    __device__ __forceinline__ void flush() {}
 };
 
 // SSSP overflow check, run only when some relaxation overflowed: an edge from
@@ -214,14 +254,13 @@ struct OverflowCheckOp {
     uint32_t* found;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = false;
-    __device__ __forceinline__ void pre(uint32_t) const {}
-    __device__ __forceinline__ uint32_t begin(uint32_t v, bool active) const {
-        return active ? __ldcg(dist + v) : INF;
-    }
-    __device__ __forceinline__ bool visit(uint32_t dv, uint32_t, uint64_t u, uint32_t) const {
+    __device__ __forceinline__ uint32_t begin(uint32_t v) { return __ldcg(dist + v); }
+    __device__ __forceinline__ uint32_t begin_chunk(uint32_t v) { return __ldcg(dist + v); }
+    __device__ __forceinline__ bool visit(uint32_t dv, uint32_t, uint64_t u, uint32_t) {
         if (dv != INF && __ldcg(dist + (uint32_t)u) == INF) atomicExch(found, 1u);
         return false;
     }
+    __device__ __forceinline__ void flush() {}
 };
 
 // ------------------------------------------------------------------ statistics
@@ -231,12 +270,46 @@ __device__ __forceinline__ void add_scanned(const Sweep& c, unsigned long long x
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(c.scanned, x);
 }
 
+// One 16-byte step of a list read: lane covers ids j and j+1 of [s, e).
+template <class Op>
+__device__ __forceinline__ void read_pair(const Sweep& c, Op& op, uint32_t st, uint32_t v, uint64_t j,
+                                          uint64_t s, uint64_t e, bool active) {
+    uint64_t u0 = 0, u1 = 0;
+    uint32_t w0 = 0, w1 = 0;
+    bool v0 = false, v1 = false;
+    if (active && j + 1 >= s) {
+        if (j + 1 < e) {
+            const ulonglong2 pr = ld_edge2(c.cols + j);
+            u0 = pr.x;
+            u1 = pr.y;
+            if (Op::kWeights) {
+                const uint2 wp = ld_w2(c.w + j);
+                w0 = wp.x;
+                w1 = wp.y;
+            }
+            v0 = j >= s;
+            v1 = true;
+        } else if (j < e && j >= s) {
+            u0 = ld_edge(c.cols + j);
+            if (Op::kWeights) w0 = ld_w(c.w + j);
+            v0 = true;
+        }
+    }
+    const bool p0 = v0 && op.visit(st, v, u0, w0);
+    const bool p1 = v1 && op.visit(st, v, u1, w1);
+    if (Op::kPush) {
+        if (p0) push(c.out_q, c.out_count, (uint32_t)u0);
+        if (p1) push(c.out_q, c.out_count, (uint32_t)u1);
+    }
+}
+
 // ------------------------------------------------------------------ kernels
 // Merged + aligned expansion with G lanes per vertex (G = 4, 8, 16, 32).
 // Loops are warp-uniform: a warp runs as many steps as its longest group.
 template <class Op, int G>
-__global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op) {
+__global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op_in) {
     constexpr int GPW = 32 / G;
+    Op op = op_in;
     const uint32_t lane = threadIdx.x & 31u, glane = lane % G, grp = lane / G;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -244,68 +317,39 @@ __global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op) {
     unsigned long long scanned = 0;
     for (uint64_t base = warp * GPW; base < k; base += nwarps * GPW) {
         const uint64_t idx = base + grp;
-        const bool has = idx < k;
-        uint32_t v = 0;
-        uint64_t s = 0, e = 0;
-        if (has) {
+        uint32_t v = 0, st = INF;
+        if (idx < k) {
             v = c.in_q ? c.in_q[idx] : (uint32_t)idx;
+            if (glane == 0) st = op.begin(v);
+        }
+        st = __shfl_sync(0xffffffffu, st, grp * G);
+        uint64_t s = 0, e = 0;
+        if (idx < k && st != INF) {
             s = c.off[v];
             e = c.off[v + 1];
-            if (glane == 0) {
-                op.pre(v);
-                scanned += e - s;
-            }
         }
         uint64_t a = aligned_start(s, c.shift);
         const uint64_t lines = e > s ? (e - a + 15) >> 4 : 0;
+        if (glane == 0) scanned += e - s;
         if (lines > c.large_lines) {
             if (glane == 0) defer(c, v, (lines + c.chunk_lines - 1) / c.chunk_lines);
             s = e = a = 0;
         }
-        uint32_t st = 0;
-        if (glane == 0) st = op.begin(v, has && e > s);
-        st = __shfl_sync(0xffffffffu, st, grp * G);
         const uint32_t steps = e > s ? (uint32_t)((e - a + 2 * G - 1) / (2 * G)) : 0u;
         const uint32_t maxsteps = __reduce_max_sync(0xffffffffu, steps);
-        for (uint32_t t = 0; t < maxsteps; t++) {
-            const uint64_t j = a + (uint64_t)t * (2 * G) + 2 * glane;
-            uint64_t u0 = 0, u1 = 0;
-            uint32_t w0 = 0, w1 = 0;
-            bool v0 = false, v1 = false;
-            if (t < steps && j + 1 >= s) {
-                if (j + 1 < e) {
-                    const ulonglong2 pr = ld_edge2(c.cols + j);
-                    u0 = pr.x;
-                    u1 = pr.y;
-                    if (Op::kWeights) {
-                        const uint2 wp = ld_w2(c.w + j);
-                        w0 = wp.x;
-                        w1 = wp.y;
-                    }
-                    v0 = j >= s;
-                    v1 = true;
-                } else if (j < e && j >= s) {
-                    u0 = ld_edge(c.cols + j);
-                    if (Op::kWeights) w0 = ld_w(c.w + j);
-                    v0 = true;
-                }
-            }
-            const bool p0 = v0 && op.visit(st, v, u0, w0);
-            const bool p1 = v1 && op.visit(st, v, u1, w1);
-            if (Op::kPush) {
-                if (p0) push(c.out_q, c.out_count, (uint32_t)u0);
-                if (p1) push(c.out_q, c.out_count, (uint32_t)u1);
-            }
-        }
+        for (uint32_t t = 0; t < maxsteps; t++)
+            read_pair(c, op, st, v, a + (uint64_t)t * (2 * G) + 2 * glane, s, e, t < steps);
     }
     add_scanned(c, scanned);
+    op.flush();
 }
 
 // Split lists: work item i of vertex lq_v[slot] covers lines
 // [i * chunk_lines, (i + 1) * chunk_lines) of its aligned list; one warp per
 // item, 16 bytes per lane (four 128-byte lines per step).
 template <class Op>
-__global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op) {
+__global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op_in) {
+    Op op = op_in;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -326,45 +370,18 @@ __global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op) {
         uint64_t ce = cs + 16ull * c.chunk_lines;
         if (ce > e) ce = e;
         uint32_t st = 0;
-        if (lane == 0) st = op.begin(v, true);
+        if (lane == 0) st = op.begin_chunk(v);
         st = __shfl_sync(0xffffffffu, st, 0);
-        for (uint64_t j0 = cs; j0 < ce; j0 += 64) {
-            const uint64_t j = j0 + 2 * lane;
-            uint64_t u0 = 0, u1 = 0;
-            uint32_t w0 = 0, w1 = 0;
-            bool v0 = false, v1 = false;
-            if (j + 1 >= s) {
-                if (j + 1 < ce) {
-                    const ulonglong2 pr = ld_edge2(c.cols + j);
-                    u0 = pr.x;
-                    u1 = pr.y;
-                    if (Op::kWeights) {
-                        const uint2 wp = ld_w2(c.w + j);
-                        w0 = wp.x;
-                        w1 = wp.y;
-                    }
-                    v0 = j >= s;
-                    v1 = true;
-                } else if (j < ce && j >= s) {
-                    u0 = ld_edge(c.cols + j);
-                    if (Op::kWeights) w0 = ld_w(c.w + j);
-                    v0 = true;
-                }
-            }
-            const bool p0 = v0 && op.visit(st, v, u0, w0);
-            const bool p1 = v1 && op.visit(st, v, u1, w1);
-            if (Op::kPush) {
-                if (p0) push(c.out_q, c.out_count, (uint32_t)u0);
-                if (p1) push(c.out_q, c.out_count, (uint32_t)u1);
-            }
-        }
+        for (uint64_t j0 = cs; j0 < ce; j0 += 64) read_pair(c, op, st, v, j0 + 2 * lane, s, ce, true);
     }
+    op.flush();
 }
 
 // The paper's "Merged" variant: one warp per vertex, lanes read consecutive
 // 8-byte entries starting at the list's own first element.
 template <class Op>
-__global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op) {
+__global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op_in) {
+    Op op = op_in;
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -372,43 +389,79 @@ __global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op) {
     unsigned long long scanned = 0;
     for (uint64_t idx = warp; idx < k; idx += nwarps) {
         const uint32_t v = c.in_q ? c.in_q[idx] : (uint32_t)idx;
-        const uint64_t s = c.off[v], e = c.off[v + 1];
         uint32_t st = 0;
-        if (lane == 0) {
-            op.pre(v);
-            scanned += e - s;
-            st = op.begin(v, e > s);
-        }
+        if (lane == 0) st = op.begin(v);
         st = __shfl_sync(0xffffffffu, st, 0);
+        if (st == INF) continue;
+        const uint64_t s = c.off[v], e = c.off[v + 1];
+        if (lane == 0) scanned += e - s;
         for (uint64_t i = s + lane; i < e; i += 32) {
             const uint64_t u = ld_edge(c.cols + i);
             const uint32_t w = Op::kWeights ? ld_w(c.w + i) : 0u;
             if (op.visit(st, v, u, w) && Op::kPush) push(c.out_q, c.out_count, (uint32_t)u);
         }
     }
+    __syncwarp();
     add_scanned(c, scanned);
+    op.flush();
 }
 
 // The paper's "Naive" variant: one thread per vertex, element by element.
 template <class Op>
-__global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op) {
+__global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
+    Op op = op_in;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t k = c.in_q ? (uint64_t)*c.in_count : (uint64_t)c.all_n;
     unsigned long long scanned = 0;
     for (uint64_t idx = tid; idx < k; idx += nt) {
         const uint32_t v = c.in_q ? c.in_q[idx] : (uint32_t)idx;
+        const uint32_t st = op.begin(v);
+        if (st == INF) continue;
         const uint64_t s = c.off[v], e = c.off[v + 1];
-        op.pre(v);
         scanned += e - s;
-        const uint32_t st = op.begin(v, e > s);
         for (uint64_t i = s; i < e; i++) {
             const uint64_t u = ld_edge(c.cols + i);
             const uint32_t w = Op::kWeights ? ld_w(c.w + i) : 0u;
             if (op.visit(st, v, u, w) && Op::kPush) push(c.out_q, c.out_count, (uint32_t)u);
         }
     }
+    __syncwarp();
     add_scanned(c, scanned);
+    op.flush();
+}
+
+// SSSP far-pile split (the near frontier is empty): every pending far vertex
+// whose distance is below the new threshold T moves to the near frontier, the
+// others stay in the far pile; vertices already expanded with their current
+// distance are dropped.  Each vertex is in the pile once, and nothing else
+// runs meanwhile, so plain flag updates suffice.
+__global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount_in, uint32_t* fq_out,
+                            uint32_t* fcount_out, uint32_t* nq_out, uint32_t* ncount_out, const uint32_t* dist,
+                            uint32_t* nflag, uint32_t* fflag, const uint32_t* xd, uint32_t T,
+                            uint32_t* far_min) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t k = *fcount_in;
+    uint32_t lmin = INF;
+    for (uint64_t base = tid - (threadIdx.x & 31); base < k; base += nt) {
+        const uint64_t i = base + (threadIdx.x & 31);
+        if (i < k) {
+            const uint32_t v = fq_in[i];
+            const uint32_t d = dist[v];
+            if (d >= xd[v]) {
+                fflag[v] = 0u;
+            } else if (d < T) {
+                fflag[v] = 0u;
+                nflag[v] = 1u;
+                push(nq_out, ncount_out, v);
+            } else {
+                lmin = d < lmin ? d : lmin;
+                push(fq_out, fcount_out, v);
+            }
+        }
+    }
+    warp_atomic_min(far_min, lmin);
 }
 
 // ------------------------------------------------------------------ small kernels
@@ -432,12 +485,23 @@ __global__ void k_init_identity(uint32_t* parent, uint32_t n) {
     for (uint64_t v = tid; v < n; v += nt) parent[v] = (uint32_t)v;
 }
 
-// label[v] = root of v (pointer jumping to the fixed point).
+// Root of x without writes.
+__device__ __forceinline__ uint32_t uf_root(const uint32_t* parent, uint32_t x) {
+    for (;;) {
+        const uint32_t px = __ldcg(parent + x);
+        if (px == x) return x;
+        x = px;
+    }
+}
+
+// label[v] = root of v.  Only roots are written here: a path-halving store
+// (which writes an ancestor that need not be the root) could land after the
+// owner of that entry stored its root and leave a non-root label behind.
 __global__ void k_compress(uint32_t* parent, uint32_t n) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = tid; v < n; v += nt) {
-        const uint32_t r = uf_find(parent, (uint32_t)v);
+        const uint32_t r = uf_root(parent, (uint32_t)v);
         __stcg(parent + v, r);
     }
 }

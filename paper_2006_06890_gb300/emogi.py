@@ -49,7 +49,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("access", ctypes.c_uint32),
                 ("granularity", ctypes.c_uint32), ("chunk_lines", ctypes.c_uint32),
                 ("timeout_ns", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
-                ("out_on_device", ctypes.c_int32), ("flags", ctypes.c_uint32)]
+                ("out_on_device", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("delta", ctypes.c_uint32), ("reserved0", ctypes.c_uint32)]
 
 
 class Stats(ctypes.Structure):
@@ -209,7 +210,7 @@ def load_graph(g, placement="host", borrow=False, with_weights=True) -> Graph:
 
 
 def _opts(access=None, granularity=0, chunk_lines=0, timeout_ns=0, stream=None, out_on_device=False,
-          time_kernels=False):
+          time_kernels=False, delta=0):
     o = Opts()
     o.struct_size = ctypes.sizeof(Opts)
     o.access = ACCESS[access] if isinstance(access, str) else int(access or 0)
@@ -220,6 +221,7 @@ def _opts(access=None, granularity=0, chunk_lines=0, timeout_ns=0, stream=None, 
         o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
     o.out_on_device = 1 if out_on_device else 0
     o.flags = OPT_TIME_KERNELS if time_kernels else 0
+    o.delta = int(delta)
     return o
 
 

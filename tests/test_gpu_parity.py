@@ -187,6 +187,31 @@ def test_repeated_calls_reuse_buffers():
                 np.testing.assert_array_equal(E.bfs(h, s)[0], oracle.bfs_g(g, s))
 
 
+@pytest.mark.parametrize("delta", [1, 7, 64, 0, 0xFFFFFFFF], ids=["d1", "d7", "d64", "auto", "bellman-ford"])
+@pytest.mark.parametrize("name", ["kron16", "urand14", "hub", "directed", "path"])
+def test_sssp_windows(name, delta):
+    """Every distance-window width gives the exact distances (the window only
+    orders the work)."""
+    g = graph(name)
+    with E.load_graph(g, placement="device") as h:
+        for s in sources(g):
+            d, st = E.sssp(h, s, delta=delta)
+            np.testing.assert_array_equal(d, oracle.sssp_g(g, s), err_msg=f"sssp src={s} delta={delta}")
+
+
+def test_sssp_zero_and_extreme_weights():
+    rng = np.random.default_rng(4)
+    n, m = 2000, 12000
+    s, d = rng.integers(0, n, size=m), rng.integers(0, n, size=m)
+    w = rng.choice(np.array([0, 1, 2, 0xFFFF, 0x7FFFFF], dtype=np.uint32), size=m)
+    g = gg.csr_from_edges(n, s, d, weights=w, symmetrize=False, dedup=False, drop_self_loops=False, sort=False)
+    g.undirected = False
+    with E.load_graph(g, placement="host") as h:
+        for src in (0, 1, 17):
+            for delta in (0, 1, 0xFFFFFFFF):
+                np.testing.assert_array_equal(E.sssp(h, src, delta=delta)[0], oracle.sssp_g(g, src))
+
+
 def test_unit_weights_sssp_equals_bfs():
     g = gg.kronecker(11, 16, seed=8)
     g.weights = np.ones(g.m, dtype=np.uint32)
