@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--degree", type=int, default=AVG_DEGREE)
     ap.add_argument("--no-variants", action="store_true", help="skip the naive/managed/device comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="profiling case: one BFS, SSSP and CC on a 2^22-vertex uniform graph (1.1 GB edges in "
+                         "pinned host memory), then exit")
     return ap.parse_args()
 
 
@@ -404,9 +407,28 @@ def reference(args):
     print(json.dumps(out), flush=True)
 
 
+def ncu_case(args):
+    """A small case for ncu captures: edges (1.1 GB) still far larger than L2,
+    a few hundred MB on the device, a few dozen launches."""
+    import torch
+    from paper_2006_06890_gb300 import _build
+    _build.build()
+    from paper_2006_06890_gb300 import emogi as E
+    g, srcs = make_graph(1 << 22, args.degree)
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    with E.load_graph(g, placement="host") as h:
+        sb = E.bfs(h, srcs[0], out=out)[1]
+        ss = E.sssp(h, srcs[0], out=out)[1]
+        sc = E.cc(h, out=out)[1]
+    print(json.dumps({"ncu_case": f"uniform n=2^22 degree {args.degree}, host placement",
+                      "bfs": sb, "sssp": ss, "cc": sc}))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.ncu_case:
+        ncu_case(args)
+    elif args.impl == "reference":
         reference(args)
     else:
         ours(args)
