@@ -192,6 +192,37 @@ const char* emogi_last_error(void);
 /* Library version string. */
 const char* emogi_version(void);
 
+/* ---- Breadth-first search without any allocation --------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot call cudaMalloc: code running while another component owns the
+ * whole device heap (a fixed arena reserved at start-up), code inside a
+ * latency-critical loop that must not block or fail on allocation, or code
+ * sharing a CUDA context whose allocator it may not touch.
+ *
+ * It computes exactly what emogi_bfs computes, but allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library call) and needs no graph handle.
+ * Its frontier queues and counters live in one fixed array inside the library
+ * of 2 * EMOGI_NOALLOC_MAX_VERTICES * 4 + 256 bytes (16 MiB + 256 bytes), which
+ * every GPU that loads the library holds until the process exits.
+ *   n            number of vertices, 1 <= n <= EMOGI_NOALLOC_MAX_VERTICES;
+ *                larger graphs are rejected with EMOGI_E_ARG
+ *   row_offsets  device uint64_t[n+1] (CSR vertex list, as emogi_load_csr)
+ *   col_idx      uint64_t[row_offsets[n]] readable by the current device:
+ *                device memory or mapped pinned host memory; 16-byte aligned
+ *   src          source vertex, < n
+ *   level        device uint32_t[n] output, as emogi_bfs
+ *   cuda_stream  cudaStream_t to run on (NULL = the legacy default stream)
+ * The call returns when the result is complete.  The first call on a device
+ * looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture.  Every call on a
+ * device shares the one array and the array keeps the previous call's
+ * contents (the call clears what must start at zero), so calls whose work
+ * overlaps on the GPU race: serialise them.
+ * Errors: EMOGI_E_ARG (size or pointer rejected), EMOGI_E_CUDA, EMOGI_E_TIMEOUT. */
+#define EMOGI_NOALLOC_MAX_VERTICES (1u << 21)
+emogi_status emogi_bfs_noalloc(uint64_t n, const uint64_t* row_offsets, const uint64_t* col_idx,
+                               uint64_t src, uint32_t* level, void* cuda_stream);
+
 /* Testing hook: make the k-th device allocation from now on (k >= 1) fail as
  * if cudaMalloc had returned out-of-memory; 0 disarms.  Lets tests exercise
  * EMOGI_E_NOMEM handling without exhausting a real GPU. */

@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
 // others stay in the far pile; vertices already expanded with their current
 // distance are dropped.  Each vertex is in the pile once, and nothing else
 // runs meanwhile, so plain flag updates suffice.
-__global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount_in, uint32_t* fq_out,
+static __global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount_in, uint32_t* fq_out,
                             uint32_t* fcount_out, uint32_t* nq_out, uint32_t* ncount_out, const uint32_t* dist,
                             uint32_t* nflag, uint32_t* fflag, const uint32_t* xd, uint32_t T,
                             uint32_t* far_min) {
@@ -466,7 +466,7 @@ __global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount_in, ui
 
 // ------------------------------------------------------------------ small kernels
 // state[v] = INF for all v, except state[src] = 0; queue = {src}.
-__global__ void k_init_single(uint32_t* state, uint32_t n, uint32_t src, uint32_t* q, uint32_t* flag,
+static __global__ void k_init_single(uint32_t* state, uint32_t n, uint32_t src, uint32_t* q, uint32_t* flag,
                               uint32_t* count) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
@@ -479,7 +479,7 @@ __global__ void k_init_single(uint32_t* state, uint32_t n, uint32_t src, uint32_
 }
 
 // parent[v] = v.
-__global__ void k_init_identity(uint32_t* parent, uint32_t n) {
+static __global__ void k_init_identity(uint32_t* parent, uint32_t n) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = tid; v < n; v += nt) parent[v] = (uint32_t)v;
@@ -497,7 +497,7 @@ __device__ __forceinline__ uint32_t uf_root(const uint32_t* parent, uint32_t x) 
 // label[v] = root of v.  Only roots are written here: a path-halving store
 // (which writes an ancestor that need not be the root) could land after the
 // owner of that entry stored its root and leave a non-root label behind.
-__global__ void k_compress(uint32_t* parent, uint32_t n) {
+static __global__ void k_compress(uint32_t* parent, uint32_t n) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t v = tid; v < n; v += nt) {
@@ -507,7 +507,7 @@ __global__ void k_compress(uint32_t* parent, uint32_t n) {
 }
 
 // Sum of out-degrees of vertices with a finite value (the TEPS numerator).
-__global__ void k_reached_edges(const uint32_t* state, const uint64_t* off, uint32_t n,
+static __global__ void k_reached_edges(const uint32_t* state, const uint64_t* off, uint32_t n,
                                 unsigned long long* out) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;

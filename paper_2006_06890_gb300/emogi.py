@@ -81,7 +81,9 @@ _SIGNATURES = [
     ("emogi_last_error", ctypes.c_char_p, []),
     ("emogi_version", ctypes.c_char_p, []),
     ("emogi_test_fail_device_alloc_after", None, [_I32]),
+    ("emogi_bfs_noalloc", _I32, [_U64, _P, _P, _U64, _P, _P]),
 ]
+NOALLOC_MAX_VERTICES = 1 << 21
 
 _lib_handle = None
 
@@ -265,3 +267,18 @@ def cc(g: Graph, out=None, **kw):
 
 def free_graph(g: Graph):
     g.free()
+
+
+def _dptr(x):
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+
+def bfs_noalloc(n, row_offsets, col_idx, src, level, stream=None):
+    """emogi_bfs_noalloc: BFS that allocates nothing, for callers that may not
+    call cudaMalloc.  `row_offsets` and `level` are device buffers (torch CUDA
+    tensors or raw device addresses) the caller owns; `col_idx` is device
+    memory or mapped pinned host memory.  Calls that overlap on the GPU share
+    one scratch array and must be serialised."""
+    s = None if stream is None else int(getattr(stream, "cuda_stream", stream))
+    _check(lib().emogi_bfs_noalloc(int(n), _dptr(row_offsets), _dptr(col_idx), int(src), _dptr(level), s))
+    return level
