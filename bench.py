@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--degree", type=int, default=AVG_DEGREE)
     ap.add_argument("--no-variants", action="store_true", help="skip the naive/managed/device comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the multi-source, batched and serving measurements")
     ap.add_argument("--ncu-case", action="store_true",
                     help="profiling case: one BFS, SSSP and CC on a 2^22-vertex uniform graph (1.1 GB edges in "
                          "pinned host memory), then exit")
@@ -189,10 +191,12 @@ def step_teps_edges(stats):
 
 
 def step_alg_bytes(stats):
-    """Algorithmic link bytes: 8 B per reached edge (BFS), 12 B per reached
-    edge (SSSP: id + weight), 8 B per edge (one CC pass)."""
+    """Algorithmic link bytes of the expansion launches: 8 B per list entry read
+    (BFS, CC) and 12 B per entry (SSSP: id + weight), over the entries the
+    launches actually process (direction-optimising BFS and sampled CC read
+    fewer entries than the reached edges; SSSP re-expands a few)."""
     sb, ss, sc = stats
-    return 8 * sb["edges_reached"] + 12 * ss["edges_reached"] + 8 * sc["edges_reached"]
+    return 8 * sb["edges_scanned"] + 12 * ss["edges_scanned"] + 8 * sc["edges_scanned"]
 
 
 def time_loop(torch, E, h, srcs, stream, steps, warmup, outs):
@@ -284,6 +288,7 @@ def ours(args):
                      "frac": round(achieved / link_peak, 4), "traffic": None,
                      "peak_source": "pinned host->device cudaMemcpy, 1 GiB, best of 6, measured in this run",
                      "algorithmic_bytes_per_step": int(alg_bytes / len(per)),
+                     "unit_bytes": "8 B per list entry read (BFS, CC), 12 B (SSSP)",
                      "expand_ms_per_step": round(expand_ms / len(per), 3),
                      "hbm_peak_measured_gbs": peaks.get("hbm_gbs")},
         "clocks": clk.summary(),
@@ -295,16 +300,18 @@ def ours(args):
         variants = {}
         for name, kw in (("naive_zero_copy", dict(placement="host", access="naive")),
                          ("merged_zero_copy", dict(placement="host", access="merged")),
+                         ("aligned_zero_copy_paper_forms", dict(placement="host", access="merged_aligned",
+                                                                top_down_only=True, cc_full_pass=True)),
                          ("managed_uvm", dict(placement="managed", access="merged_aligned")),
                          ("device_hbm", dict(placement="device", access="merged_aligned"))):
             try:
                 hv = h if kw["placement"] == "host" else E.load_graph(g, placement=kw["placement"])
-                acc = kw["access"]
+                okw = {k: v for k, v in kw.items() if k != "placement"}
 
                 def one(src):
-                    sb = E.bfs(hv, src, stream=stream, access=acc, out=outs[0])[1]
-                    ss = E.sssp(hv, src, stream=stream, access=acc, out=outs[1])[1]
-                    sc = E.cc(hv, stream=stream, access=acc, out=outs[2])[1]
+                    sb = E.bfs(hv, src, stream=stream, out=outs[0], **okw)[1]
+                    ss = E.sssp(hv, src, stream=stream, out=outs[1], **okw)[1]
+                    sc = E.cc(hv, stream=stream, out=outs[2], **okw)[1]
                     return (sb, ss, sc)
 
                 t0 = time.perf_counter()
@@ -323,6 +330,14 @@ def ours(args):
                 variants[name] = {"error": str(ex)[:200]}
         result["variants"] = variants
 
+    # ---- multi-source BFS, batched many-graph BFS and serving (rank 0)
+    if rank == 0 and not args.no_extras:
+        for name, fn in (("msbfs", extra_msbfs), ("batch", extra_batch), ("serving", extra_serving)):
+            try:
+                result[name] = fn(E, torch)
+            except Exception as ex:  # noqa: BLE001 - report, keep the bench line
+                result[name] = {"error": str(ex)[:300]}
+
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(g, srcs[0])
@@ -333,6 +348,151 @@ def ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def _time(torch, fn, stream):
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t0 = time.perf_counter()
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3, r
+
+
+def extra_msbfs(E, torch):
+    """64 BFS sources in one multi-source pass vs 64 single BFS calls on an
+    undirected Kronecker graph (scale 24, edge factor 16) in pinned host memory."""
+    import graphgen as gg
+    g = gg.kronecker(24, 16, seed=GEN_SEED)
+    srcs = [int(s) for s in gg.random_sources(g, 64, seed=SRC_SEED)]
+    st = torch.cuda.Stream()
+    out = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+    one = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    with E.load_graph(g, placement="host") as h:
+        E.msbfs(h, srcs[:4], out=out, stream=st)  # warm-up
+        ms_ms, _, (lv, sm) = _time(torch, lambda: E.msbfs(h, srcs, out=out, stream=st), st)
+        E.bfs(h, srcs[0], out=one, stream=st)
+        seq = []
+        ms_seq, _, _ = _time(torch, lambda: [seq.append(E.bfs(h, s, out=one, stream=st)[1]) for s in srcs], st)
+        ms_td, _, _ = _time(torch, lambda: [E.bfs(h, s, out=one, stream=st, top_down_only=True) for s in srcs],
+                            st)
+    reached = sm["edges_reached"]
+    return {"workload": f"Kronecker scale 24 ef 16 (n={g.n}, m={g.m}), 64 seeded sources, host placement",
+            "msbfs_ms": round(ms_ms, 2), "msbfs_gteps": round(reached / (ms_ms * 1e-3) / 1e9, 3),
+            "msbfs_levels": sm["iterations"], "msbfs_edges_read": sm["edges_scanned"],
+            "single_bfs_64_ms": round(ms_seq, 2), "single_bfs_gteps": round(reached / (ms_seq * 1e-3) / 1e9, 3),
+            "single_bfs_top_down_64_ms": round(ms_td, 2),
+            "speedup_vs_single": round(ms_seq / ms_ms, 3),
+            "edges_read_single": int(sum(x["edges_scanned"] for x in seq))}
+
+
+def extra_batch(E, torch):
+    """512 uneven uniform-random graphs (2^10..2^18 vertices log-uniform,
+    average degree 4..64) in HBM: one persistent graph-captured batched BFS vs
+    512 single BFS calls, after the autotuner picks lanes per vertex and claim."""
+    import graphgen as gg
+    rng = np.random.default_rng(4)
+    gs = []
+    for i in range(512):
+        n = int(2 ** rng.uniform(10, 18))
+        gs.append(gg.uniform(n, int(rng.integers(4, 65)), seed=4000 + i))
+    srcs = [gg.max_degree_vertex(g) for g in gs]
+    hs = [E.load_graph(g, placement="device") for g in gs]
+    st = torch.cuda.Stream()
+    try:
+        with E.Batch(hs) as b:
+            out = torch.empty(b.total, dtype=torch.int32, device="cuda")
+            G, claim, tune_ms = b.autotune(srcs)
+            b.bfs(srcs, out=out)
+            reps = 5
+            ms_b, _, stats = _time(torch, lambda: [b.bfs(srcs, out=out)[1] for _ in range(reps)], st)
+            ms_b /= reps
+            reached = stats[-1]["edges_reached"]
+        one = torch.empty(max(g.n for g in gs), dtype=torch.int32, device="cuda")
+        for h, s in zip(hs[:8], srcs[:8]):
+            E.bfs(h, s, out=one, stream=st)
+        ms_s, _, _ = _time(torch, lambda: [E.bfs(h, s, out=one, stream=st) for h, s in zip(hs, srcs)], st)
+    finally:
+        for h in hs:
+            h.free()
+    return {"workload": f"512 uniform graphs, sum n={sum(g.n for g in gs)}, sum m={sum(g.m for g in gs)}, "
+                        "device placement",
+            "autotuned": {"granularity": G, "claim": claim, "ms": round(tune_ms, 3)},
+            "batch_ms": round(ms_b, 3), "batch_queries_per_s": round(512 / (ms_b * 1e-3), 1),
+            "batch_gteps": round(reached / (ms_b * 1e-3) / 1e9, 3),
+            "single_calls_ms": round(ms_s, 3), "single_queries_per_s": round(512 / (ms_s * 1e-3), 1),
+            "speedup_vs_single": round(ms_s / ms_b, 3)}
+
+
+def extra_serving(E, torch):
+    """Poisson-arriving BFS (80 %) and SSSP (20 %) queries with seeded random
+    sources over a resident set (Kronecker scales 16, 18, 20 and uniform 2^18,
+    2^20, degree 16; the two smallest in HBM, the rest in pinned host memory),
+    results discarded; p50/p99 latency and throughput per offered load, next
+    to the same queries run one at a time."""
+    import graphgen as gg
+    specs = [("kron16", lambda: gg.kronecker(16, 16, seed=11, weights=True), "device"),
+             ("urand18", lambda: gg.uniform(1 << 18, 16, seed=12, weights=True), "device"),
+             ("kron18", lambda: gg.kronecker(18, 16, seed=13, weights=True), "host"),
+             ("kron20", lambda: gg.kronecker(20, 16, seed=14, weights=True), "host"),
+             ("urand20", lambda: gg.uniform(1 << 20, 16, seed=15, weights=True), "host")]
+    gs, hs = [], []
+    for _, mk, place in specs:
+        g = mk()
+        gs.append(g)
+        hs.append(E.load_graph(g, placement=place))
+    rng = np.random.default_rng(3)
+    out = {"workload": "resident set " + ", ".join(f"{nm} ({pl})" for nm, _, pl in specs)}
+    try:
+        def make_queries(count):
+            qs = []
+            for _ in range(count):
+                gi = int(rng.integers(0, len(gs)))
+                qs.append((gi, "bfs" if rng.random() < 0.8 else "sssp", int(rng.integers(0, gs[gi].n))))
+            return qs
+
+        # one query at a time through the plain calls
+        base_q = make_queries(300)
+        st = torch.cuda.Stream()
+        outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in gs]
+        t0 = time.perf_counter()
+        lat = []
+        for gi, kind, src in base_q:
+            t1 = time.perf_counter()
+            (E.bfs if kind == "bfs" else E.sssp)(hs[gi], src, out=outs[gi], stream=st)
+            lat.append((time.perf_counter() - t1) * 1e3)
+        wall = time.perf_counter() - t0
+        out["one_at_a_time"] = {"queries_per_s": round(len(base_q) / wall, 1),
+                                "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                                "p99_ms": round(float(np.percentile(lat, 99)), 3)}
+        loads = []
+        with E.Server(max_slots=4) as srv:
+            for rate in (1000, 5000, 20000):
+                qs = make_queries(2000)
+                gaps = rng.exponential(1.0 / rate, size=len(qs))
+                tickets = []
+                t0 = time.perf_counter()
+                t_next = t0
+                for (gi, kind, src), gap in zip(qs, gaps):
+                    t_next += gap
+                    while time.perf_counter() < t_next:
+                        pass
+                    tickets.append(srv.submit(hs[gi], kind, src))
+                res = [srv.wait(t) for t in tickets]
+                wall = time.perf_counter() - t0
+                lat = np.array([r["latency_ms"] for r in res])
+                loads.append({"offered_qps": rate, "achieved_qps": round(len(qs) / wall, 1),
+                              "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                              "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                              "mean_batch": round(float(np.mean([r["batch_size"] for r in res])), 2),
+                              "max_batch": int(max(r["batch_size"] for r in res))})
+        out["loads"] = loads
+    finally:
+        for h in hs:
+            h.free()
+    return out
 
 
 def oracle_step(g, src):

@@ -77,8 +77,14 @@ typedef enum {
 
 /* emogi_opts.flags */
 enum {
-    EMOGI_OPT_TIME_KERNELS = 1u << 0 /* bracket every neighbour-expansion launch with CUDA events and
-                                        report their summed duration in emogi_stats.expand_ms */
+    EMOGI_OPT_TIME_KERNELS = 1u << 0, /* bracket every neighbour-expansion launch with CUDA events and
+                                         report their summed duration in emogi_stats.expand_ms */
+    EMOGI_OPT_TOP_DOWN_ONLY = 1u << 1, /* BFS: expand every level from the frontier (push) as the paper
+                                          does, never switch an undirected graph's dense levels to the
+                                          bottom-up (pull) direction */
+    EMOGI_OPT_CC_FULL_PASS = 1u << 2   /* CC: stream the whole edge list as the paper does instead of
+                                          linking sampled neighbours first and skipping the vertices
+                                          already in the largest sampled component */
 };
 
 /* Per-call options.  Pass NULL for defaults.  struct_size must be
@@ -136,6 +142,13 @@ emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets,
 /* Breadth-first search from src (Sec. 2.1, Algorithm "High-level Graph
  * Traversal Flow" with the BFS condition: an unvisited neighbour of an active
  * vertex becomes active at the next depth; one kernel round per level, Sec. 4.2).
+ * On graphs loaded with EMOGI_LOAD_UNDIRECTED and MERGED_ALIGNED access, a
+ * level whose frontier holds more edges than 1/14 of the unreached vertices'
+ * edges is expanded bottom-up instead (every unreached vertex reads its own
+ * list up to its first neighbour on the current level) until the frontier
+ * falls below n/24 vertices (direction-optimising BFS, Beamer et al. 2012);
+ * EMOGI_OPT_TOP_DOWN_ONLY keeps the paper's push-only form.  The levels are
+ * the same either way.
  *   level  uint32_t[n] output (host, or device if opts->out_on_device):
  *          level[src] = 0, hop distance for reached vertices, EMOGI_INF otherwise.
  * Errors: EMOGI_E_ARG (src >= n, NULL pointer), EMOGI_E_BUDGET, EMOGI_E_NOMEM,
@@ -156,14 +169,118 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
                         emogi_stats* stats);
 
 /* Connected components of an undirected graph (Sec. 5.4: every vertex starts
- * active and the entire edge list is streamed).  One pass over all edges
- * hooks the larger union-find root under the smaller with compare-and-swap,
- * then pointer jumping resolves every vertex to its root.
+ * active and the entire edge list is streamed).  Edges hook the larger
+ * union-find root under the smaller with compare-and-swap, then every vertex
+ * is resolved to its root.  By default the edge stream is sampled first
+ * (Afforest, Sutton et al. 2018): each vertex is linked with its first two
+ * neighbours, the largest resulting tree is found from 1024 samples, and only
+ * vertices outside it read their lists; EMOGI_OPT_CC_FULL_PASS streams every
+ * list as the paper does.  The labels are the same either way.
  *   label  uint32_t[n] output: the smallest vertex id of the vertex's component.
  * Errors: EMOGI_E_UNSUPPORTED if the graph was not loaded with
  * EMOGI_LOAD_UNDIRECTED (the paper runs CC on undirected graphs only), and
  * the errors of emogi_bfs. */
 emogi_status emogi_cc(emogi_graph g, uint32_t* label, const emogi_opts* opts, emogi_stats* stats);
+
+/* Multi-source BFS: k independent BFS traversals (1 <= k <= 64) in one
+ * level-synchronous pass.  Each vertex carries 64-bit masks (visited, in the
+ * frontier, reached this level), bit b for source b, so one read of a
+ * neighbour list serves every source whose frontier holds the vertex.  The
+ * paper runs its BFS from 64 sources one at a time (Sec. 5.2); the result
+ * here is identical to k separate emogi_bfs calls.
+ *   srcs    host uint64_t[k], each < n (repeats allowed)
+ *   levels  uint32_t[k * n] output, row b = the levels from srcs[b] (host, or
+ *           device if opts->out_on_device)
+ * Errors: EMOGI_E_ARG (k out of range, a source >= n, NULL pointer) and the
+ * errors of emogi_bfs. */
+emogi_status emogi_msbfs(emogi_graph g, const uint64_t* srcs, uint32_t k, uint32_t* levels,
+                         const emogi_opts* opts, emogi_stats* stats);
+
+/* ---- Batched BFS over many graphs in one persistent launch ----------------
+ * The paper traverses one graph per run with one kernel launch per level
+ * (Sec. 4.2).  A batch advances every graph of a set by one level per round
+ * of a single cooperatively launched, persistent kernel: the frontiers of all
+ * graphs form one queue of (graph, vertex) entries that warps claim in
+ * chunks, and rounds are separated by a grid-wide barrier whose wait is
+ * bounded by opts->timeout_ns (EMOGI_E_TIMEOUT when exceeded).  Source upload,
+ * initialisation and the persistent kernel are recorded once as a CUDA graph
+ * and replayed on every call.  Results equal one emogi_bfs per graph.
+ *
+ * emogi_batch_create: graphs[0..count) are loaded graphs on one device (any
+ *   placement); the batch keeps the handles (free it before them) and
+ *   allocates its combined queues and levels (about 20 bytes per vertex).
+ * emogi_batch_bfs: srcs host uint64_t[count], srcs[g] < n of graph g;
+ *   levels uint32_t[emogi_batch_total_vertices(b)] output (host, or device if
+ *   opts->out_on_device): graph g's levels start at emogi_batch_offset(b, g).
+ *   opts->granularity = lanes per vertex (0 = the batch's current choice),
+ *   opts->chunk_lines = frontier entries a warp claims at once, in units of
+ *   its lane groups (0 = current choice).  Only MERGED_ALIGNED access.
+ * emogi_batch_autotune: runs the batch from srcs with every lanes-per-vertex
+ *   choice {4, 8, 16, 32} and claim size {1, 4, 16, 64}, keeps the fastest as
+ *   the batch's choice and reports it (any output pointer may be NULL).
+ * emogi_bfs_batch: one-shot create + bfs + free.
+ * Errors: EMOGI_E_ARG (NULL, empty graph, mixed devices, a source out of
+ * range), EMOGI_E_UNSUPPORTED (access other than MERGED_ALIGNED),
+ * EMOGI_E_TIMEOUT, EMOGI_E_BUDGET, EMOGI_E_NOMEM, EMOGI_E_CUDA. */
+typedef struct emogi_batch_s* emogi_batch;
+emogi_status emogi_batch_create(const emogi_graph* graphs, uint32_t count, emogi_batch* out);
+emogi_status emogi_batch_bfs(emogi_batch b, const uint64_t* srcs, uint32_t* levels, const emogi_opts* opts,
+                             emogi_stats* stats);
+emogi_status emogi_batch_autotune(emogi_batch b, const uint64_t* srcs, uint32_t* best_granularity,
+                                  uint32_t* best_claim, double* best_ms);
+uint64_t emogi_batch_offset(emogi_batch b, uint32_t g);
+uint64_t emogi_batch_total_vertices(emogi_batch b);
+emogi_status emogi_batch_free(emogi_batch b);
+emogi_status emogi_bfs_batch(const emogi_graph* graphs, const uint64_t* srcs, uint32_t* levels, uint32_t count,
+                             const emogi_opts* opts, emogi_stats* stats);
+
+/* ---- Query server with continuous batching --------------------------------
+ * The paper runs one traversal at a time.  A server accepts BFS and SSSP
+ * queries over already loaded graphs from any thread and runs them on
+ * max_slots worker slots, each with its own CUDA stream and its own share
+ * (emogi_graph_share) of every graph it serves, so jobs overlap on the GPU.
+ * When a slot is idle the oldest pending query forms the next job; a BFS job
+ * also takes the other pending BFS queries of the same graph (up to
+ * max_batch) and runs them as one multi-source pass (emogi_msbfs), so queries
+ * that arrive while others run join the next pass.  A job is admitted only
+ * when the device bytes the slots hold (their traversal buffers, kept
+ * resident between jobs, and the batch's level rows, k * n * 4 bytes) fit
+ * device_budget; idle slots release their buffers first, a job that does not
+ * fit waits for running ones, and one that cannot fit on an idle server
+ * fails with EMOGI_E_BUDGET.  Results equal the single-query calls.
+ *   emogi_server_submit: out is a host uint32_t[n] for the result, or NULL to
+ *     discard it; it must stay valid until the query is waited for.  The
+ *     graph must outlive the server.
+ *   emogi_server_wait: blocks until the query is done (timeout_ns = 0: no
+ *     limit; otherwise EMOGI_E_TIMEOUT when it is not done in time, and the
+ *     ticket stays valid), fills *res and releases the ticket; returns the
+ *     query's own status.
+ *   emogi_server_drain: waits until every submitted query is done.
+ *   emogi_server_destroy: drains, stops the workers and frees their buffers. */
+typedef struct emogi_server_s* emogi_server;
+typedef enum { EMOGI_QUERY_BFS = 0, EMOGI_QUERY_SSSP = 1 } emogi_query_kind;
+typedef struct {
+    uint32_t struct_size;
+    uint32_t max_slots;      /* worker slots; 0 = 4, at most 64 */
+    uint64_t device_budget;  /* bytes the slots' buffers may hold; 0 = unlimited */
+    uint32_t max_batch;      /* BFS queries per multi-source pass, 1..64; 0 = 64 */
+    uint32_t reserved;
+} emogi_server_config;
+typedef struct {
+    emogi_status status;
+    uint32_t batch_size;     /* queries that ran in the same job */
+    double queue_ms;         /* submit -> job start */
+    double run_ms;           /* job start -> result ready */
+    double latency_ms;       /* submit -> result ready */
+    uint64_t edges_reached;  /* TEPS numerator (a batch reports its mean per query) */
+} emogi_query_result;
+emogi_status emogi_server_create(const emogi_server_config* cfg, emogi_server* out);
+emogi_status emogi_server_submit(emogi_server s, emogi_graph g, uint32_t kind, uint64_t src, uint32_t* out,
+                                 uint64_t* ticket);
+emogi_status emogi_server_wait(emogi_server s, uint64_t ticket, uint64_t timeout_ns, emogi_query_result* res);
+emogi_status emogi_server_drain(emogi_server s);
+uint64_t emogi_server_device_bytes(emogi_server s);
+emogi_status emogi_server_destroy(emogi_server s);
 
 /* Set the device-memory budget in bytes for all graphs and work buffers the
  * library allocates from now on (0 = unlimited).  Allocations that would
@@ -177,6 +294,16 @@ uint64_t emogi_device_bytes_in_use(void);
 /* Release a graph and every buffer the library holds for it.  NULL is a no-op.
  * Returns EMOGI_E_CUDA if a CUDA free failed (the handle is released anyway). */
 emogi_status emogi_free_graph(emogi_graph g);
+
+/* A second handle onto a loaded graph: it reads the same row offsets, edge
+ * list and weights (nothing is copied) but has its own stream and work
+ * buffers, so that traversals through different handles of one graph can run
+ * concurrently from different threads.  Free every share before the original
+ * handle.  Errors: EMOGI_E_ARG, EMOGI_E_NOMEM, EMOGI_E_CUDA. */
+emogi_status emogi_graph_share(emogi_graph g, emogi_graph* out);
+
+/* Device bytes of the work buffers this handle holds (0 before its first traversal). */
+uint64_t emogi_graph_workspace_bytes(emogi_graph g);
 
 /* Properties of a loaded graph. */
 uint64_t emogi_graph_num_vertices(emogi_graph g);

@@ -131,6 +131,7 @@ emogi_status ensure_workspace(emogi_graph g) {
         {(void**)&ws.xd, n * 4, "expanded distances"},
         {(void**)&ws.lq_v, ws.lq_cap * 4, "split-list vertices"},
         {(void**)&ws.lq_base, ws.lq_cap * 8, "split-list chunk bases"},
+        {(void**)&ws.lq_state, ws.lq_cap * 8, "split-list states"},
         {(void**)&ws.ctr, sizeof(DevCounters), "counters"},
     };
     for (auto& it : items) {
@@ -164,6 +165,11 @@ void release_workspace(emogi_graph g) {
     dev_free(ws.xd, ws.n * 4);
     dev_free(ws.lq_v, ws.lq_cap * 4);
     dev_free(ws.lq_base, ws.lq_cap * 8);
+    dev_free(ws.lq_state, ws.lq_cap * 8);
+    dev_free(ws.ms_visit, ws.n * 8);
+    dev_free(ws.ms_front, ws.n * 8);
+    dev_free(ws.ms_next, ws.n * 8);
+    dev_free(ws.ms_out, ws.ms_out_bytes);
     dev_free(ws.ctr, sizeof(DevCounters));
     // dev_free's accounting assumes the sizes it was allocated with; when a
     // partial allocation failed, unallocated entries are null and skipped.
@@ -409,15 +415,48 @@ emogi_status emogi_free_graph(emogi_graph g) {
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
     release_workspace(g);
-    release_array(g->place, g->cols_owned, g->cols_borrowed, g->m * sizeof(uint64_t));
-    if (g->w || g->w_owned || g->w_borrowed) release_array(g->place, g->w_owned, g->w_borrowed, g->m * sizeof(uint32_t));
-    if (g->d_off) dev_free(g->d_off, (g->n + 1) * sizeof(uint64_t));
+    if (!g->shared) {
+        release_array(g->place, g->cols_owned, g->cols_borrowed, g->m * sizeof(uint64_t));
+        if (g->w || g->w_owned || g->w_borrowed)
+            release_array(g->place, g->w_owned, g->w_borrowed, g->m * sizeof(uint32_t));
+        if (g->d_off) dev_free(g->d_off, (g->n + 1) * sizeof(uint64_t));
+    }
     cudaError_t e = cudaSuccess;
     if (g->stream) e = cudaStreamDestroy(g->stream);
     delete g;
     if (e != cudaSuccess) return fail(EMOGI_E_CUDA, "cudaStreamDestroy: %s", cudaGetErrorString(e));
     return EMOGI_OK;
 }
+
+emogi_status emogi_graph_share(emogi_graph g, emogi_graph* out) {
+    clear_error();
+    if (!g || !out) return fail(EMOGI_E_ARG, "graph and out must be non-NULL");
+    *out = nullptr;
+    emogi_graph h = new (std::nothrow) emogi_graph_s();
+    if (!h) return fail(EMOGI_E_NOMEM, "graph handle");
+    h->device = g->device;
+    h->n = g->n;
+    h->m = g->m;
+    h->flags = g->flags;
+    h->place = g->place;
+    h->d_off = g->d_off;
+    h->cols = g->cols;
+    h->w = g->w;
+    h->shift = g->shift;
+    h->avg_degree = g->avg_degree;
+    h->avg_weight = g->avg_weight;
+    h->shared = true;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        delete h;
+        return fail(EMOGI_E_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    *out = h;
+    return EMOGI_OK;
+}
+
+uint64_t emogi_graph_workspace_bytes(emogi_graph g) { return g ? g->ws.dev_bytes : 0; }
 
 uint64_t emogi_graph_num_vertices(emogi_graph g) { return g ? g->n : 0; }
 uint64_t emogi_graph_num_edges(emogi_graph g) { return g ? g->m : 0; }

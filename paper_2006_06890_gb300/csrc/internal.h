@@ -64,6 +64,9 @@ struct DevCounters {
     unsigned long long large[2];     // split-list work: (slots << 34) | items
     unsigned long long scanned;      // neighbour entries read
     unsigned long long reached;      // sum of out-degrees of reached vertices
+    unsigned long long fedges;       // BFS: sum of out-degrees of the next frontier
+    uint32_t giant;                  // sampled CC: root of the largest sampled tree
+    uint32_t pad2;
 };
 
 struct Workspace {
@@ -77,11 +80,18 @@ struct Workspace {
     bool flags_dirty = false;              // a call ended early and left flags set
     uint32_t* lq_v = nullptr;              // split-list vertices
     unsigned long long* lq_base = nullptr; // first chunk index of each split-list vertex
+    unsigned long long* lq_state = nullptr;// the split-list vertex's per-sweep value
     uint64_t lq_cap = 0;
     DevCounters* ctr = nullptr;
     DevCounters* h_ctr = nullptr;          // pinned mirror for readback
     size_t dev_bytes = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // multi-source BFS state, allocated on first use
+    unsigned long long* ms_visit = nullptr;  // sources that reached v
+    unsigned long long* ms_front = nullptr;  // sources for which v is in the frontier
+    unsigned long long* ms_next = nullptr;   // sources reaching v in the sweep under way
+    uint32_t* ms_out = nullptr;              // k x n levels when the output is on the host
+    size_t ms_out_bytes = 0;
 };
 
 }  // namespace emogi
@@ -104,6 +114,7 @@ struct emogi_graph_s {
     emogi::Workspace ws;
     double avg_degree = 0.0;
     double avg_weight = 0.0;           // mean of a sample of the weights
+    bool shared = false;               // a view made by emogi_graph_share: the arrays belong to another handle
 };
 
 namespace emogi {

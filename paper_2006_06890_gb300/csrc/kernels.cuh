@@ -37,21 +37,22 @@ constexpr unsigned long long CHUNK_MASK = (1ull << SLOT_SHIFT) - 1;
 
 // Everything a sweep needs besides the per-application state.
 struct Sweep {
-    const uint64_t* off;       // row offsets (GPU memory)
-    const uint64_t* cols;      // edge list (GPU, pinned host or managed memory)
-    const uint32_t* w;         // weights beside the edges, or null
-    uint32_t shift;            // (edge-list base address mod 128) / 8
-    const uint32_t* in_q;      // active vertices, or null for "all vertices"
-    const uint32_t* in_count;  // number of active vertices (when in_q != null)
-    uint32_t all_n;            // number of vertices (when in_q == null)
-    uint32_t* out_q;           // next active vertices
-    uint32_t* out_count;
-    uint32_t* lq_v;            // split-list queue: vertex
-    unsigned long long* lq_base;   // split-list queue: first work item
-    unsigned long long* large;     // (slots << 34) | items
-    uint32_t large_lines;      // lists with more lines than this are split
-    uint32_t chunk_lines;      // lines per split work item
-    unsigned long long* scanned;   // neighbour entries read (statistics)
+    const uint64_t* off = nullptr;       // row offsets (GPU memory)
+    const uint64_t* cols = nullptr;      // edge list (GPU, pinned host or managed memory)
+    const uint32_t* w = nullptr;         // weights beside the edges, or null
+    uint32_t shift = 0;                  // (edge-list base address mod 128) / 8
+    const uint32_t* in_q = nullptr;      // active vertices, or null for "all vertices"
+    const uint32_t* in_count = nullptr;  // number of active vertices (when in_q != null)
+    uint32_t all_n = 0;                  // number of vertices (when in_q == null)
+    uint32_t* out_q = nullptr;           // next active vertices
+    uint32_t* out_count = nullptr;
+    uint32_t* lq_v = nullptr;                      // split-list queue: vertex
+    unsigned long long* lq_base = nullptr;         // split-list queue: first work item
+    unsigned long long* lq_state = nullptr;        // split-list queue: the vertex's begin() value
+    unsigned long long* large = nullptr;           // (slots << 34) | items
+    uint32_t large_lines = 0xFFFFFFFFu;  // lists with more lines than this are split
+    uint32_t chunk_lines = 1;            // lines per split work item
+    unsigned long long* scanned = nullptr;         // neighbour entries read (statistics)
 };
 
 // ------------------------------------------------------------------ loads
@@ -110,39 +111,58 @@ __device__ __forceinline__ void push(uint32_t* q, uint32_t* count, uint32_t v) {
 
 // Append a long list to the split-list queue: one 64-bit atomic hands out both
 // the slot and the first work item, so bases increase with slot numbers.
-__device__ __forceinline__ void defer(const Sweep& c, uint32_t v, unsigned long long items) {
+__device__ __forceinline__ void defer(const Sweep& c, uint32_t v, unsigned long long items,
+                                     unsigned long long st) {
     unsigned long long old = atomicAdd(c.large, (1ull << SLOT_SHIFT) | items);
     unsigned long long slot = old >> SLOT_SHIFT;
     c.lq_v[slot] = v;
     c.lq_base[slot] = old & CHUNK_MASK;
+    c.lq_state[slot] = st;
 }
 
 // ------------------------------------------------------------------ applications
 // The per-neighbour work of a sweep is a policy object.  Each thread works on
 // its own copy, so a policy may keep per-thread accumulators.
+//   S, kSkip       the per-vertex value type broadcast to the lanes reading a
+//                  list, and the value meaning "do not read this list";
 //   begin(v)       one lane per active vertex, before the list is read: returns
-//                  the 32-bit value broadcast to the lanes reading v's list, or
-//                  INF to skip the list entirely;
-//   begin_chunk(v) the same for one work item of a split (long) list;
+//                  that value (a split list's items reuse it);
 //   visit(st,v,u,w) the update for edge (v, u) with weight w; true = push u to
 //                  the next frontier;
 //   flush()        once per thread at kernel end, whole warp converged.
 
+// Warp-reduced atomic add of a per-thread count (whole warp converged).
+__device__ __forceinline__ void warp_atomic_add(unsigned long long* out, unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(out, x);
+}
+
 // BFS (Sec. 2.1): an unvisited neighbour gets the next level and becomes active.
-// The compare-and-swap makes exactly one visitor push it.
+// The compare-and-swap makes exactly one visitor push it.  When `off` is set,
+// the out-degrees of the vertices pushed are summed into `fedges` (the edge
+// count of the next frontier, which picks the direction of the next level).
 struct BfsOp {
     uint32_t* level;
     uint32_t next;
+    const uint64_t* off = nullptr;
+    unsigned long long* fedges = nullptr;
+    unsigned long long lf = 0;
+    using S = uint32_t;
+    static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = true;
-    __device__ __forceinline__ uint32_t begin(uint32_t) { return 0; }
-    __device__ __forceinline__ uint32_t begin_chunk(uint32_t) { return 0; }
-    __device__ __forceinline__ bool visit(uint32_t, uint32_t, uint64_t u, uint32_t) {
+    __device__ __forceinline__ S begin(uint32_t) { return 0; }
+    __device__ __forceinline__ bool visit(S, uint32_t, uint64_t u, uint32_t) {
         uint32_t* p = level + (uint32_t)u;
         if (*p != INF) return false;
-        return atomicCAS(p, INF, next) == INF;
+        if (atomicCAS(p, INF, next) != INF) return false;
+        if (off) lf += off[(uint32_t)u + 1] - off[(uint32_t)u];
+        return true;
     }
-    __device__ __forceinline__ void flush() {}
+    __device__ __forceinline__ void flush() {
+        if (fedges) warp_atomic_add(fedges, lf);
+    }
 };
 
 // Warp-reduced atomic minimum of a per-thread value (whole warp converged).
@@ -174,9 +194,11 @@ struct SsspOp {
     uint32_t* overflow;
     uint32_t T;
     uint32_t lmin;  // per-thread smallest distance sent to the far pile
+    using S = uint32_t;
+    static constexpr S kSkip = INF;
     static constexpr bool kWeights = true;
     static constexpr bool kPush = true;
-    __device__ __forceinline__ uint32_t begin(uint32_t v) {
+    __device__ __forceinline__ S begin(uint32_t v) {
         atomicExch(nflag + v, 0u);
         __threadfence();
         const uint32_t d = __ldcg(dist + v);
@@ -184,7 +206,6 @@ struct SsspOp {
         __stcg(xd + v, d);
         return d;
     }
-    __device__ __forceinline__ uint32_t begin_chunk(uint32_t v) { return __ldcg(dist + v); }
     // A relaxation whose sum does not fit below INF is dropped and noted; the
     // host then checks whether some reachable vertex was left at INF.
     __device__ __forceinline__ bool visit(uint32_t dv, uint32_t, uint64_t u64, uint32_t w) {
@@ -208,6 +229,35 @@ struct SsspOp {
     __device__ __forceinline__ void flush() { warp_atomic_min(far_min, lmin); }
 };
 
+// Multi-source BFS over up to 64 sources at once: bit b of a vertex's masks
+// belongs to source b.  One read of a list serves every source whose frontier
+// holds the vertex: the neighbour gains the frontier bits it has not been
+// visited by (visit is fixed during a sweep), collected with an atomic OR; the
+// first OR that lands on an empty mask queues the neighbour.
+struct MsBfsOp {
+    unsigned long long* front;
+    const unsigned long long* seen;  // visit masks
+    unsigned long long* next;
+    using S = unsigned long long;
+    static constexpr S kSkip = 0ull;
+    static constexpr bool kWeights = false;
+    static constexpr bool kPush = true;
+    __device__ __forceinline__ S begin(uint32_t v) {
+        const S f = front[v];
+        if (f) front[v] = 0ull;  // each vertex is queued once per sweep
+        return f;
+    }
+    __device__ __forceinline__ bool visit_edge(S f, uint64_t u64) {
+        const uint32_t u = (uint32_t)u64;
+        const S nb = f & ~seen[u];
+        if (!nb) return false;
+        if ((next[u] & nb) == nb) return false;  // a stale read only shows fewer bits
+        return atomicOr(next + u, nb) == 0ull;
+    }
+    __device__ __forceinline__ bool visit(S f, uint32_t, uint64_t u, uint32_t) { return visit_edge(f, u); }
+    __device__ __forceinline__ void flush() {}
+};
+
 // Union-find root with path halving.  Parents only ever point to smaller ids
 // and a non-root never becomes a root again, so racing halving stores always
 // write an ancestor.  Reads bypass L1 so that hooks made by other SMs are seen.
@@ -227,11 +277,12 @@ __device__ __forceinline__ uint32_t uf_find(uint32_t* parent, uint32_t x) {
 // of every component is its smallest vertex id.
 struct CcOp {
     uint32_t* parent;
+    using S = uint32_t;
+    static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = false;
-    __device__ __forceinline__ uint32_t begin(uint32_t) { return 0; }
-    __device__ __forceinline__ uint32_t begin_chunk(uint32_t) { return 0; }
-    __device__ __forceinline__ bool visit(uint32_t, uint32_t v, uint64_t u64, uint32_t) {
+    __device__ __forceinline__ S begin(uint32_t) { return 0; }
+    __device__ __forceinline__ bool visit(S, uint32_t v, uint64_t u64, uint32_t) {
         uint32_t u = (uint32_t)u64;
         if (u >= v) return false;
         uint32_t a = v, b = u;
@@ -246,17 +297,56 @@ struct CcOp {
     __device__ __forceinline__ void flush() {}
 };
 
+// Sampled CC (Afforest, Sutton, Ben-Nun and Barak, IPDPS 2018), final pass:
+// vertices already joined to the sampled largest tree (parent == giant) are
+// skipped; every other vertex links itself with each of its neighbours, in
+// either id order, because its neighbour may have been skipped.  Skipping is
+// safe: a skipped vertex's parent pointer already ties it to the giant tree,
+// and each edge to a vertex outside that tree is linked from the other end.
+struct CcFinalOp {
+    uint32_t* parent;
+    uint32_t giant;
+    using S = uint32_t;
+    static constexpr S kSkip = INF;
+    static constexpr bool kWeights = false;
+    static constexpr bool kPush = false;
+    __device__ __forceinline__ S begin(uint32_t v) { return __ldcg(parent + v) == giant ? kSkip : 0u; }
+    __device__ __forceinline__ bool visit(S, uint32_t v, uint64_t u64, uint32_t) {
+        uint32_t a = v, b = (uint32_t)u64;
+        for (;;) {
+            a = uf_find(parent, a);
+            b = uf_find(parent, b);
+            if (a == b) return false;
+            const uint32_t hi = a > b ? a : b, lo = a > b ? b : a;
+            if (atomicCAS(parent + hi, hi, lo) == hi) return false;
+        }
+    }
+    __device__ __forceinline__ void flush() {}
+};
+
+// Union of a and b (larger root under the smaller).
+__device__ __forceinline__ void uf_union(uint32_t* parent, uint32_t a, uint32_t b) {
+    for (;;) {
+        a = uf_find(parent, a);
+        b = uf_find(parent, b);
+        if (a == b) return;
+        const uint32_t hi = a > b ? a : b, lo = a > b ? b : a;
+        if (atomicCAS(parent + hi, hi, lo) == hi) return;
+    }
+}
+
 // SSSP overflow check, run only when some relaxation overflowed: an edge from
 // a vertex with a finite distance to one left at INF means that neighbour is
 // reachable but its shortest distance does not fit below UINT32_MAX.
 struct OverflowCheckOp {
     const uint32_t* dist;
     uint32_t* found;
+    using S = uint32_t;
+    static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = false;
-    __device__ __forceinline__ uint32_t begin(uint32_t v) { return __ldcg(dist + v); }
-    __device__ __forceinline__ uint32_t begin_chunk(uint32_t v) { return __ldcg(dist + v); }
-    __device__ __forceinline__ bool visit(uint32_t dv, uint32_t, uint64_t u, uint32_t) {
+    __device__ __forceinline__ S begin(uint32_t v) { return __ldcg(dist + v); }
+    __device__ __forceinline__ bool visit(S dv, uint32_t, uint64_t u, uint32_t) {
         if (dv != INF && __ldcg(dist + (uint32_t)u) == INF) atomicExch(found, 1u);
         return false;
     }
@@ -270,38 +360,50 @@ __device__ __forceinline__ void add_scanned(const Sweep& c, unsigned long long x
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(c.scanned, x);
 }
 
-// One 16-byte step of a list read: lane covers ids j and j+1 of [s, e).
+// One 16-byte step of a list read: the lane covers ids j and j+1 of [s, e).
+// Loading and visiting are split so that a lane can issue several steps'
+// loads before it waits on the first (more 16-byte requests in flight).
+struct PairLoad {
+    ulonglong2 id;
+    uint2 w;
+    uint32_t valid;  // bit 0: id j, bit 1: id j + 1
+};
+
 template <class Op>
-__device__ __forceinline__ void read_pair(const Sweep& c, Op& op, uint32_t st, uint32_t v, uint64_t j,
-                                          uint64_t s, uint64_t e, bool active) {
-    uint64_t u0 = 0, u1 = 0;
-    uint32_t w0 = 0, w1 = 0;
-    bool v0 = false, v1 = false;
+__device__ __forceinline__ PairLoad load_pair(const Sweep& c, uint64_t j, uint64_t s, uint64_t e, bool active) {
+    PairLoad p;
+    p.id = make_ulonglong2(0, 0);
+    p.w = make_uint2(0, 0);
+    p.valid = 0;
     if (active && j + 1 >= s) {
         if (j + 1 < e) {
-            const ulonglong2 pr = ld_edge2(c.cols + j);
-            u0 = pr.x;
-            u1 = pr.y;
-            if (Op::kWeights) {
-                const uint2 wp = ld_w2(c.w + j);
-                w0 = wp.x;
-                w1 = wp.y;
-            }
-            v0 = j >= s;
-            v1 = true;
+            p.id = ld_edge2(c.cols + j);
+            if (Op::kWeights) p.w = ld_w2(c.w + j);
+            p.valid = (j >= s ? 1u : 0u) | 2u;
         } else if (j < e && j >= s) {
-            u0 = ld_edge(c.cols + j);
-            if (Op::kWeights) w0 = ld_w(c.w + j);
-            v0 = true;
+            p.id.x = ld_edge(c.cols + j);
+            if (Op::kWeights) p.w.x = ld_w(c.w + j);
+            p.valid = 1u;
         }
     }
-    const bool p0 = v0 && op.visit(st, v, u0, w0);
-    const bool p1 = v1 && op.visit(st, v, u1, w1);
+    return p;
+}
+
+template <class Op>
+__device__ __forceinline__ void visit_pair(const Sweep& c, Op& op, typename Op::S st, uint32_t v, const PairLoad& p) {
+    const bool p0 = (p.valid & 1u) && op.visit(st, v, p.id.x, p.w.x);
+    const bool p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y);
     if (Op::kPush) {
-        if (p0) push(c.out_q, c.out_count, (uint32_t)u0);
-        if (p1) push(c.out_q, c.out_count, (uint32_t)u1);
+        if (p0) push(c.out_q, c.out_count, (uint32_t)p.id.x);
+        if (p1) push(c.out_q, c.out_count, (uint32_t)p.id.y);
     }
 }
+
+// Steps whose loads a lane issues back to back before visiting them.
+#ifndef EMOGI_PIPELINE_STEPS
+#define EMOGI_PIPELINE_STEPS 4
+#endif
+constexpr int kSteps = EMOGI_PIPELINE_STEPS;
 
 // ------------------------------------------------------------------ kernels
 // Merged + aligned expansion with G lanes per vertex (G = 4, 8, 16, 32).
@@ -317,14 +419,15 @@ __global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op_in) {
     unsigned long long scanned = 0;
     for (uint64_t base = warp * GPW; base < k; base += nwarps * GPW) {
         const uint64_t idx = base + grp;
-        uint32_t v = 0, st = INF;
+        uint32_t v = 0;
+        typename Op::S st = Op::kSkip;
         if (idx < k) {
             v = c.in_q ? c.in_q[idx] : (uint32_t)idx;
             if (glane == 0) st = op.begin(v);
         }
         st = __shfl_sync(0xffffffffu, st, grp * G);
         uint64_t s = 0, e = 0;
-        if (idx < k && st != INF) {
+        if (idx < k && st != Op::kSkip) {
             s = c.off[v];
             e = c.off[v + 1];
         }
@@ -332,13 +435,19 @@ __global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op_in) {
         const uint64_t lines = e > s ? (e - a + 15) >> 4 : 0;
         if (glane == 0) scanned += e - s;
         if (lines > c.large_lines) {
-            if (glane == 0) defer(c, v, (lines + c.chunk_lines - 1) / c.chunk_lines);
+            if (glane == 0) defer(c, v, (lines + c.chunk_lines - 1) / c.chunk_lines, (unsigned long long)st);
             s = e = a = 0;
         }
         const uint32_t steps = e > s ? (uint32_t)((e - a + 2 * G - 1) / (2 * G)) : 0u;
         const uint32_t maxsteps = __reduce_max_sync(0xffffffffu, steps);
-        for (uint32_t t = 0; t < maxsteps; t++)
-            read_pair(c, op, st, v, a + (uint64_t)t * (2 * G) + 2 * glane, s, e, t < steps);
+        for (uint32_t t0 = 0; t0 < maxsteps; t0 += kSteps) {
+            PairLoad p[kSteps];
+#pragma unroll
+            for (int u = 0; u < kSteps; u++)
+                p[u] = load_pair<Op>(c, a + (uint64_t)(t0 + u) * (2 * G) + 2 * glane, s, e, t0 + u < steps);
+#pragma unroll
+            for (int u = 0; u < kSteps; u++) visit_pair(c, op, st, v, p[u]);
+        }
     }
     add_scanned(c, scanned);
     op.flush();
@@ -369,12 +478,73 @@ __global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op_in) {
         const uint64_t cs = a + ci * 16ull * c.chunk_lines;
         uint64_t ce = cs + 16ull * c.chunk_lines;
         if (ce > e) ce = e;
-        uint32_t st = 0;
-        if (lane == 0) st = op.begin_chunk(v);
-        st = __shfl_sync(0xffffffffu, st, 0);
-        for (uint64_t j0 = cs; j0 < ce; j0 += 64) read_pair(c, op, st, v, j0 + 2 * lane, s, ce, true);
+        const typename Op::S st = (typename Op::S)c.lq_state[lo];
+        for (uint64_t j0 = cs; j0 < ce; j0 += 64 * kSteps) {
+            PairLoad p[kSteps];
+#pragma unroll
+            for (int u = 0; u < kSteps; u++) p[u] = load_pair<Op>(c, j0 + 64 * u + 2 * lane, s, ce, true);
+#pragma unroll
+            for (int u = 0; u < kSteps; u++) visit_pair(c, op, st, v, p[u]);
+        }
     }
     op.flush();
+}
+
+// Bottom-up BFS sweep (the pull direction of direction-optimising BFS, Beamer,
+// Asanovic and Patterson, SC 2012), for undirected graphs: every vertex not yet
+// reached reads its own list, G lanes per vertex in aligned 16-byte steps, and
+// stops at the first neighbour on level L; it then takes level L + 1 and joins
+// the next frontier.  When most vertices are already reached this reads a
+// small prefix of few lists instead of every list of a huge frontier.
+// Only the owner writes level[v], and a vertex set to L + 1 during this sweep
+// never reads as L, so plain accesses suffice.
+template <int G>
+__global__ void __launch_bounds__(256) k_bfs_bottom_up(Sweep c, uint32_t* level, uint32_t L,
+                                                       unsigned long long* fedges) {
+    constexpr int GPW = 32 / G;
+    const uint32_t lane = threadIdx.x & 31u, glane = lane % G, grp = lane / G;
+    const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (grp * G);
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t n = c.all_n;
+    unsigned long long scanned = 0, lf = 0;
+    for (uint64_t base = warp * GPW; base < n; base += nwarps * GPW) {
+        const uint64_t v = base + grp;
+        uint64_t s = 0, e = 0;
+        if (v < n && level[v] == INF) {
+            s = c.off[v];
+            e = c.off[v + 1];
+        }
+        const uint64_t a = aligned_start(s, c.shift);
+        const uint32_t steps = e > s ? (uint32_t)((e - a + 2 * G - 1) / (2 * G)) : 0u;
+        bool found = false;
+        for (uint32_t t = 0; __any_sync(0xffffffffu, t < steps && !found); t++) {
+            bool hit = false;
+            if (t < steps && !found) {
+                const uint64_t j = a + (uint64_t)t * (2 * G) + 2 * glane;
+                if (j + 1 >= s) {
+                    if (j + 1 < e) {
+                        const ulonglong2 pr = ld_edge2(c.cols + j);
+                        hit = (j >= s && level[(uint32_t)pr.x] == L) || level[(uint32_t)pr.y] == L;
+                        scanned += (j >= s) ? 2 : 1;
+                    } else if (j < e && j >= s) {
+                        hit = level[(uint32_t)ld_edge(c.cols + j)] == L;
+                        scanned += 1;
+                    }
+                }
+            }
+            // every lane must reach the ballot: evaluate it before combining
+            const unsigned hits = __ballot_sync(0xffffffffu, hit);
+            found = found || (hits & gmask) != 0;
+        }
+        if (found && glane == 0) {
+            level[v] = L + 1;
+            lf += e - s;
+            push(c.out_q, c.out_count, (uint32_t)v);
+        }
+    }
+    add_scanned(c, scanned);
+    warp_atomic_add(fedges, lf);
 }
 
 // The paper's "Merged" variant: one warp per vertex, lanes read consecutive
@@ -389,10 +559,10 @@ __global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op_in) {
     unsigned long long scanned = 0;
     for (uint64_t idx = warp; idx < k; idx += nwarps) {
         const uint32_t v = c.in_q ? c.in_q[idx] : (uint32_t)idx;
-        uint32_t st = 0;
+        typename Op::S st = Op::kSkip;
         if (lane == 0) st = op.begin(v);
         st = __shfl_sync(0xffffffffu, st, 0);
-        if (st == INF) continue;
+        if (st == Op::kSkip) continue;
         const uint64_t s = c.off[v], e = c.off[v + 1];
         if (lane == 0) scanned += e - s;
         for (uint64_t i = s + lane; i < e; i += 32) {
@@ -416,8 +586,8 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
     unsigned long long scanned = 0;
     for (uint64_t idx = tid; idx < k; idx += nt) {
         const uint32_t v = c.in_q ? c.in_q[idx] : (uint32_t)idx;
-        const uint32_t st = op.begin(v);
-        if (st == INF) continue;
+        const typename Op::S st = op.begin(v);
+        if (st == Op::kSkip) continue;
         const uint64_t s = c.off[v], e = c.off[v + 1];
         scanned += e - s;
         for (uint64_t i = s; i < e; i++) {
@@ -504,6 +674,106 @@ static __global__ void k_compress(uint32_t* parent, uint32_t n) {
         const uint32_t r = uf_root(parent, (uint32_t)v);
         __stcg(parent + v, r);
     }
+}
+
+// Multi-source BFS, end of a sweep: each newly reached vertex takes its new
+// bits into visit and into its frontier mask, and level L is written for each
+// new (source, vertex) pair; levels is k rows of n entries.
+static __global__ void k_ms_finalize(const uint32_t* q, const uint32_t* count, unsigned long long* visit,
+                                     unsigned long long* front, unsigned long long* next, uint32_t* levels,
+                                     uint64_t n, uint32_t level) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t k = *count;
+    for (uint64_t i = tid; i < k; i += nt) {
+        const uint32_t u = q[i];
+        unsigned long long nb = next[u];
+        next[u] = 0ull;
+        visit[u] |= nb;
+        front[u] = nb;
+        while (nb) {
+            const int b = __ffsll((long long)nb) - 1;
+            nb &= nb - 1;
+            levels[(uint64_t)b * n + u] = level;
+        }
+    }
+}
+
+struct MsSources {
+    uint32_t v[64];
+    uint32_t k;
+};
+
+// Multi-source BFS start: source b sets bit b of its vertex and level 0 in
+// row b; each distinct source vertex is queued once.
+static __global__ void k_ms_init(MsSources src, unsigned long long* visit, unsigned long long* front,
+                                 uint32_t* levels, uint64_t n, uint32_t* q, uint32_t* count) {
+    const uint32_t b = threadIdx.x;
+    if (b >= src.k) return;
+    const uint32_t s = src.v[b];
+    const unsigned long long bit = 1ull << b;
+    atomicOr(visit + s, bit);
+    const unsigned long long old = atomicOr(front + s, bit);
+    levels[(uint64_t)b * n + s] = 0;
+    if (old == 0ull) q[atomicAdd(count, 1u)] = s;
+}
+
+// Sum over vertices of out-degree x number of sources that reached it.
+static __global__ void k_ms_reached_edges(const unsigned long long* visit, const uint64_t* off, uint32_t n,
+                                          unsigned long long* out) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    unsigned long long acc = 0;
+    for (uint64_t v = tid; v < n; v += nt) acc += (off[v + 1] - off[v]) * (unsigned long long)__popcll(visit[v]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
+}
+
+// Sampled CC, first phase: every vertex is linked with its first `rounds`
+// neighbours (one or two ids, usually one 32-byte sector of the edge list).
+static __global__ void k_cc_sample(const uint64_t* off, const uint64_t* cols, uint32_t* parent, uint32_t n,
+                                   uint32_t rounds, unsigned long long* scanned) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    unsigned long long cnt = 0;
+    for (uint64_t v = tid; v < n; v += nt) {
+        const uint64_t s = off[v], e = off[v + 1];
+        const uint64_t k = e - s < rounds ? e - s : rounds;
+        for (uint64_t r = 0; r < k; r++) uf_union(parent, (uint32_t)v, (uint32_t)ld_edge(cols + s + r));
+        cnt += k;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(scanned, cnt);
+}
+
+// Sampled CC: the most frequent root among up to 1024 sample vertices of
+// non-zero degree (one block of 1024 threads), written to *giant.
+static __global__ void k_cc_giant(const uint32_t* parent, const uint64_t* off, uint32_t n, uint32_t* giant) {
+    __shared__ uint32_t root[1024];
+    __shared__ unsigned long long best;
+    const uint32_t t = threadIdx.x;
+    if (t == 0) best = 0;
+    uint32_t r = INF;
+    // sample vertex t * stride, stepping forward to the first vertex with edges
+    const uint64_t stride = n > 1024 ? n / 1024 : 1;
+    uint64_t v = (uint64_t)t * stride;
+    for (uint32_t tries = 0; v < n && tries < 64; tries++, v++) {
+        if (off[v + 1] > off[v]) {
+            r = __ldcg(parent + v);
+            break;
+        }
+    }
+    root[t] = r;
+    __syncthreads();
+    uint32_t cnt = 0;
+    if (r != INF)
+        for (uint32_t i = 0; i < 1024; i++) cnt += root[i] == r;
+    // the largest count wins; ties go to the smaller root id
+    if (r != INF) atomicMax(&best, ((unsigned long long)cnt << 32) | (unsigned long long)(0xFFFFFFFFu - r));
+    __syncthreads();
+    if (t == 0) *giant = best ? 0xFFFFFFFFu - (uint32_t)(best & 0xFFFFFFFFu) : INF;
 }
 
 // Sum of out-degrees of vertices with a finite value (the TEPS numerator).

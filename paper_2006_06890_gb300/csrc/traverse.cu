@@ -85,6 +85,7 @@ Sweep make_sweep(const Ctx& c, int side, bool all_vertices) {
     s.out_count = &ws.ctr->qcount[side ^ 1];
     s.lq_v = ws.lq_v;
     s.lq_base = ws.lq_base;
+    s.lq_state = ws.lq_state;
     s.large = &ws.ctr->large[0];
     s.large_lines = kLargeLines;
     s.chunk_lines = c.chunk;
@@ -122,6 +123,25 @@ emogi_status sweep(Ctx& c, const Sweep& s, const Op& op, uint64_t k) {
     }
     EMOGI_CUDA_TRY(cudaGetLastError());
     if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[3], c.st));
+    c.expand_launches++;
+    return EMOGI_OK;
+}
+
+// One bottom-up BFS sweep over all vertices at level L.
+emogi_status sweep_bottom_up(Ctx& c, const Sweep& s, uint32_t* level, uint32_t L) {
+    Workspace& ws = c.g->ws;
+    const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
+    if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
+    const uint32_t G = std::min<uint32_t>(c.G, 8);
+    const int grid = grid_for(c, (uint64_t)c.g->n * G);
+    unsigned long long* fe = &ws.ctr->fedges;
+    switch (G) {
+        case 4: dev::k_bfs_bottom_up<4><<<grid, kThreads, 0, c.st>>>(s, level, L, fe); break;
+        default: dev::k_bfs_bottom_up<8><<<grid, kThreads, 0, c.st>>>(s, level, L, fe); break;
+    }
+    EMOGI_CUDA_TRY(cudaGetLastError());
+    if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[3], c.st));
+    c.kernel_launches++;
     c.expand_launches++;
     return EMOGI_OK;
 }
@@ -235,9 +255,38 @@ emogi_status emogi_bfs(emogi_graph g, uint64_t src, uint32_t* level, const emogi
                                                                   nullptr, &ws.ctr->qcount[0]);
     EMOGI_CUDA_TRY(cudaGetLastError());
     c.kernel_launches++;
-    uint32_t iters = 0;
-    EMOGI_TRY(level_loop(c, [&](uint32_t next) { return dev::BfsOp{state, next}; }, &iters));
-    return finish(c, state, level, true, iters, stats, false);
+    // direction choice of Beamer et al.: go bottom-up when the frontier's edges
+    // exceed 1/14 of the unreached vertices' edges, back to top-down when the
+    // frontier holds fewer than n/24 vertices
+    const bool diropt = (g->flags & EMOGI_LOAD_UNDIRECTED) && !(c.o.flags & EMOGI_OPT_TOP_DOWN_ONLY) &&
+                        c.o.access == EMOGI_ACCESS_MERGED_ALIGNED;
+    int side = 0;
+    uint64_t nf = 1, mf = 0, mu = g->m;
+    bool top_down = true;
+    uint32_t it = 0;
+    while (nf > 0) {
+        if (it > g->n + 1) return fail(EMOGI_E_TIMEOUT, "BFS did not converge in %u levels", it);
+        if (diropt && it > 0) {
+            if (top_down && mf > mu / 14) top_down = false;
+            else if (!top_down && nf < g->n / 24) top_down = true;
+        }
+        EMOGI_TRY(reset_sweep_counters(c, side));
+        EMOGI_CUDA_TRY(cudaMemsetAsync(&ws.ctr->fedges, 0, sizeof(unsigned long long), c.st));
+        Sweep s = make_sweep(c, side, !top_down);
+        if (top_down) {
+            dev::BfsOp op{state, it + 1, diropt ? g->d_off : nullptr, diropt ? &ws.ctr->fedges : nullptr};
+            EMOGI_TRY(sweep(c, s, op, nf));
+        } else {
+            EMOGI_TRY(sweep_bottom_up(c, s, state, it));
+        }
+        EMOGI_TRY(read_counters(c));
+        nf = ws.h_ctr->qcount[side ^ 1];
+        mf = ws.h_ctr->fedges;
+        mu -= std::min(mu, mf);
+        side ^= 1;
+        it++;
+    }
+    return finish(c, state, level, true, it, stats, false);
 }
 
 emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi_opts* opts, emogi_stats* stats) {
@@ -322,6 +371,96 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
     return finish(c, state, dist, true, it, stats, true);
 }
 
+emogi_status emogi_msbfs(emogi_graph g, const uint64_t* srcs, uint32_t k, uint32_t* levels, const emogi_opts* opts,
+                         emogi_stats* stats) {
+    clear_error();
+    Ctx c;
+    EMOGI_TRY(setup(g, opts, &c));
+    if (k < 1 || k > EMOGI_MAX_SOURCES) return fail(EMOGI_E_ARG, "k = %u sources; 1 to 64 are supported", k);
+    if (!srcs) return fail(EMOGI_E_ARG, "srcs is NULL");
+    dev::MsSources ms;
+    ms.k = k;
+    for (uint32_t b = 0; b < k; b++) {
+        if (srcs[b] >= g->n)
+            return fail(EMOGI_E_ARG, "source %u = %llu is not below n = %llu", b, (unsigned long long)srcs[b],
+                        (unsigned long long)g->n);
+        ms.v[b] = (uint32_t)srcs[b];
+    }
+    EMOGI_TRY(check_output(g, c.o, levels));
+    Workspace& ws = g->ws;
+    const uint64_t n = g->n;
+    if (!ws.ms_visit) {
+        EMOGI_TRY(dev_alloc((void**)&ws.ms_visit, n * 8, "multi-source visit masks"));
+        EMOGI_TRY(dev_alloc((void**)&ws.ms_front, n * 8, "multi-source frontier masks"));
+        EMOGI_TRY(dev_alloc((void**)&ws.ms_next, n * 8, "multi-source next masks"));
+    }
+    uint32_t* out = levels;
+    if (!c.o.out_on_device) {
+        const size_t need = (size_t)k * n * 4;
+        if (ws.ms_out_bytes < need) {
+            dev_free(ws.ms_out, ws.ms_out_bytes);
+            ws.ms_out = nullptr;
+            ws.ms_out_bytes = 0;
+            EMOGI_TRY(dev_alloc((void**)&ws.ms_out, need, "multi-source levels"));
+            ws.ms_out_bytes = need;
+        }
+        out = ws.ms_out;
+    }
+    EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[0], c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ctr, 0, sizeof(DevCounters), c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ms_visit, 0, n * 8, c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ms_front, 0, n * 8, c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ms_next, 0, n * 8, c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(out, 0xFF, (size_t)k * n * 4, c.st));
+    dev::k_ms_init<<<1, 64, 0, c.st>>>(ms, ws.ms_visit, ws.ms_front, out, n, ws.q[0], &ws.ctr->qcount[0]);
+    EMOGI_CUDA_TRY(cudaGetLastError());
+    c.kernel_launches++;
+    EMOGI_TRY(read_counters(c, false));
+    uint64_t kq = ws.h_ctr->qcount[0];
+    int side = 0;
+    uint32_t it = 0;
+    while (kq > 0) {
+        if (it > n + 1) return fail(EMOGI_E_TIMEOUT, "multi-source BFS did not converge in %u levels", it);
+        EMOGI_TRY(reset_sweep_counters(c, side));
+        Sweep s = make_sweep(c, side, false);
+        EMOGI_TRY(sweep(c, s, dev::MsBfsOp{ws.ms_front, ws.ms_visit, ws.ms_next}, kq));
+        dev::k_ms_finalize<<<grid_for(c, n), kThreads, 0, c.st>>>(ws.q[side ^ 1], &ws.ctr->qcount[side ^ 1],
+                                                                   ws.ms_visit, ws.ms_front, ws.ms_next, out, n,
+                                                                   it + 1);
+        EMOGI_CUDA_TRY(cudaGetLastError());
+        c.kernel_launches++;
+        EMOGI_TRY(read_counters(c));
+        kq = ws.h_ctr->qcount[side ^ 1];
+        side ^= 1;
+        it++;
+    }
+    if (stats && n) {
+        dev::k_ms_reached_edges<<<grid_for(c, n), kThreads, 0, c.st>>>(ws.ms_visit, g->d_off, (uint32_t)n,
+                                                                         &ws.ctr->reached);
+        EMOGI_CUDA_TRY(cudaGetLastError());
+        c.kernel_launches++;
+    }
+    EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[1], c.st));
+    if (!c.o.out_on_device)
+        EMOGI_CUDA_TRY(cudaMemcpyAsync(levels, out, (size_t)k * n * 4, cudaMemcpyDeviceToHost, c.st));
+    EMOGI_CUDA_TRY(cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c.st));
+    EMOGI_CUDA_TRY(cudaStreamSynchronize(c.st));
+    if (stats) {
+        float ms = 0.f;
+        EMOGI_CUDA_TRY(cudaEventElapsedTime(&ms, ws.ev[0], ws.ev[1]));
+        memset(stats, 0, sizeof *stats);
+        stats->iterations = it;
+        stats->edges_scanned = ws.h_ctr->scanned;
+        stats->edges_reached = ws.h_ctr->reached;
+        stats->edge_bytes = ws.h_ctr->scanned * 8ull;
+        stats->ms = ms;
+        stats->expand_ms = c.expand_ms;
+        stats->expand_launches = c.expand_launches;
+        stats->kernel_launches = c.kernel_launches;
+    }
+    return EMOGI_OK;
+}
+
 emogi_status emogi_cc(emogi_graph g, uint32_t* label, const emogi_opts* opts, emogi_stats* stats) {
     clear_error();
     Ctx c;
@@ -333,17 +472,38 @@ emogi_status emogi_cc(emogi_graph g, uint32_t* label, const emogi_opts* opts, em
     uint32_t* parent = c.o.out_on_device ? label : ws.state;
     EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[0], c.st));
     EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ctr, 0, sizeof(DevCounters), c.st));
+    const bool sampled = !(c.o.flags & EMOGI_OPT_CC_FULL_PASS) && c.o.access == EMOGI_ACCESS_MERGED_ALIGNED;
     if (g->n) {
-        dev::k_init_identity<<<grid_for(c, g->n), kThreads, 0, c.st>>>(parent, (uint32_t)g->n);
+        const uint32_t n = (uint32_t)g->n;
+        dev::k_init_identity<<<grid_for(c, n), kThreads, 0, c.st>>>(parent, n);
         EMOGI_CUDA_TRY(cudaGetLastError());
+        c.kernel_launches++;
         Sweep s = make_sweep(c, 0, true);
-        EMOGI_TRY(sweep(c, s, dev::CcOp{parent}, g->n));
-        dev::k_compress<<<grid_for(c, g->n), kThreads, 0, c.st>>>(parent, (uint32_t)g->n);
+        if (sampled) {
+            const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
+            if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
+            dev::k_cc_sample<<<grid_for(c, n), kThreads, 0, c.st>>>(g->d_off, g->cols, parent, n, 2,
+                                                                     &ws.ctr->scanned);
+            EMOGI_CUDA_TRY(cudaGetLastError());
+            if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[3], c.st));
+            c.expand_launches++;
+            if (timed) EMOGI_TRY(read_counters(c));
+            dev::k_compress<<<grid_for(c, n), kThreads, 0, c.st>>>(parent, n);
+            dev::k_cc_giant<<<1, 1024, 0, c.st>>>(parent, g->d_off, n, &ws.ctr->giant);
+            EMOGI_CUDA_TRY(cudaGetLastError());
+            EMOGI_TRY(read_counters(c, false));
+            c.kernel_launches += 3;
+            EMOGI_TRY(reset_sweep_counters(c, 0));
+            EMOGI_TRY(sweep(c, s, dev::CcFinalOp{parent, ws.h_ctr->giant}, n));
+        } else {
+            EMOGI_TRY(sweep(c, s, dev::CcOp{parent}, n));
+        }
+        dev::k_compress<<<grid_for(c, n), kThreads, 0, c.st>>>(parent, n);
         EMOGI_CUDA_TRY(cudaGetLastError());
-        c.kernel_launches += 2;  // identity init + compress
+        c.kernel_launches++;
         if (c.o.flags & EMOGI_OPT_TIME_KERNELS) EMOGI_TRY(read_counters(c));
     }
-    return finish(c, parent, label, false, 1, stats, false);
+    return finish(c, parent, label, false, sampled ? 2 : 1, stats, false);
 }
 
 }  // extern "C"

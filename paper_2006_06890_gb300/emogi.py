@@ -33,6 +33,8 @@ ACCESS = {"merged_aligned": ACCESS_MERGED_ALIGNED, "aligned": ACCESS_MERGED_ALIG
           "merged": ACCESS_MERGED, "naive": ACCESS_NAIVE}
 # opts flags
 OPT_TIME_KERNELS = 1
+OPT_TOP_DOWN_ONLY = 2
+OPT_CC_FULL_PASS = 4
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -71,17 +73,34 @@ _SIGNATURES = [
     ("emogi_bfs", _I32, [_P, _U64, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
     ("emogi_sssp", _I32, [_P, _U64, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
     ("emogi_cc", _I32, [_P, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+    ("emogi_msbfs", _I32, [_P, _P, _U32, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
     ("emogi_set_device_budget", _I32, [_U64]),
     ("emogi_device_bytes_in_use", _U64, []),
     ("emogi_free_graph", _I32, [_P]),
     ("emogi_graph_num_vertices", _U64, [_P]),
     ("emogi_graph_num_edges", _U64, [_P]),
     ("emogi_graph_placement", _I32, [_P]),
+    ("emogi_graph_share", _I32, [_P, ctypes.POINTER(_P)]),
+    ("emogi_graph_workspace_bytes", _U64, [_P]),
     ("emogi_status_string", ctypes.c_char_p, [_I32]),
     ("emogi_last_error", ctypes.c_char_p, []),
     ("emogi_version", ctypes.c_char_p, []),
     ("emogi_test_fail_device_alloc_after", None, [_I32]),
     ("emogi_bfs_noalloc", _I32, [_U64, _P, _P, _U64, _P, _P]),
+    ("emogi_batch_create", _I32, [_P, _U32, ctypes.POINTER(_P)]),
+    ("emogi_batch_bfs", _I32, [_P, _P, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+    ("emogi_batch_autotune", _I32, [_P, _P, ctypes.POINTER(_U32), ctypes.POINTER(_U32),
+                                    ctypes.POINTER(ctypes.c_double)]),
+    ("emogi_batch_offset", _U64, [_P, _U32]),
+    ("emogi_batch_total_vertices", _U64, [_P]),
+    ("emogi_batch_free", _I32, [_P]),
+    ("emogi_bfs_batch", _I32, [_P, _P, _P, _U32, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+    ("emogi_server_create", _I32, [ctypes.c_void_p, ctypes.POINTER(_P)]),
+    ("emogi_server_submit", _I32, [_P, _P, _U32, _U64, _P, ctypes.POINTER(_U64)]),
+    ("emogi_server_wait", _I32, [_P, _U64, _U64, ctypes.c_void_p]),
+    ("emogi_server_drain", _I32, [_P]),
+    ("emogi_server_device_bytes", _U64, [_P]),
+    ("emogi_server_destroy", _I32, [_P]),
 ]
 NOALLOC_MAX_VERTICES = 1 << 21
 
@@ -168,6 +187,15 @@ class Graph:
             _check(lib().emogi_free_graph(h))
             self._keepalive = ()
 
+    def share(self):
+        """emogi_graph_share: another handle on the same arrays with its own buffers."""
+        h = ctypes.c_void_p()
+        _check(lib().emogi_graph_share(self.handle, ctypes.byref(h)))
+        return Graph(h.value, self.n, self.m, self.placement, (self,))
+
+    def workspace_bytes(self) -> int:
+        return int(lib().emogi_graph_workspace_bytes(self.handle))
+
     def __enter__(self):
         return self
 
@@ -212,7 +240,7 @@ def load_graph(g, placement="host", borrow=False, with_weights=True) -> Graph:
 
 
 def _opts(access=None, granularity=0, chunk_lines=0, timeout_ns=0, stream=None, out_on_device=False,
-          time_kernels=False, delta=0):
+          time_kernels=False, delta=0, top_down_only=False, cc_full_pass=False):
     o = Opts()
     o.struct_size = ctypes.sizeof(Opts)
     o.access = ACCESS[access] if isinstance(access, str) else int(access or 0)
@@ -222,7 +250,8 @@ def _opts(access=None, granularity=0, chunk_lines=0, timeout_ns=0, stream=None, 
     if stream is not None:
         o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
     o.out_on_device = 1 if out_on_device else 0
-    o.flags = OPT_TIME_KERNELS if time_kernels else 0
+    o.flags = (OPT_TIME_KERNELS if time_kernels else 0) | (OPT_TOP_DOWN_ONLY if top_down_only else 0) | \
+        (OPT_CC_FULL_PASS if cc_full_pass else 0)
     o.delta = int(delta)
     return o
 
@@ -265,6 +294,27 @@ def cc(g: Graph, out=None, **kw):
     return _run(lib().emogi_cc, g, (), out, kw)
 
 
+def msbfs(g: Graph, sources, out=None, **kw):
+    """emogi_msbfs -> (levels of shape (k, n), stats dict); row b is the BFS from sources[b]."""
+    srcs = np.ascontiguousarray(np.asarray(sources, dtype=np.uint64).ravel())
+    k = int(srcs.size)
+    if out is None:
+        arr = np.empty((k, max(g.n, 1)), dtype=np.uint32)
+        ptr, res, on_dev = arr.ctypes.data, arr[:, :g.n], False
+    elif hasattr(out, "data_ptr"):
+        if out.numel() < k * g.n or out.element_size() != 4 or not out.is_contiguous():
+            raise EmogiError(E_ARG, "output tensor must be contiguous, 4-byte and hold k * n entries")
+        ptr, res, on_dev = out.data_ptr(), out, bool(out.is_cuda)
+    else:
+        if out.dtype != np.uint32 or out.size < k * g.n or not out.flags.c_contiguous:
+            raise EmogiError(E_ARG, "output array must be contiguous uint32 with k * n entries")
+        ptr, res, on_dev = out.ctypes.data, out, False
+    o = _opts(out_on_device=on_dev, **kw)
+    s = Stats()
+    _check(lib().emogi_msbfs(g.handle, srcs.ctypes.data, k, ptr, ctypes.byref(o), ctypes.byref(s)))
+    return res, s.as_dict()
+
+
 def free_graph(g: Graph):
     g.free()
 
@@ -282,3 +332,153 @@ def bfs_noalloc(n, row_offsets, col_idx, src, level, stream=None):
     s = None if stream is None else int(getattr(stream, "cuda_stream", stream))
     _check(lib().emogi_bfs_noalloc(int(n), _dptr(row_offsets), _dptr(col_idx), int(src), _dptr(level), s))
     return level
+
+
+class Batch:
+    """A set of loaded graphs traversed together (emogi_batch_*)."""
+
+    def __init__(self, graphs):
+        self.graphs = list(graphs)
+        arr = (ctypes.c_void_p * len(self.graphs))(*[g.handle.value for g in self.graphs])
+        h = ctypes.c_void_p()
+        _check(lib().emogi_batch_create(ctypes.cast(arr, ctypes.c_void_p), len(self.graphs), ctypes.byref(h)))
+        self._h = h
+        self.total = int(lib().emogi_batch_total_vertices(h))
+        self.offsets = [int(lib().emogi_batch_offset(h, i)) for i in range(len(self.graphs))]
+
+    def _srcs(self, sources):
+        s = np.ascontiguousarray(np.asarray(sources, dtype=np.uint64).ravel())
+        if s.size != len(self.graphs):
+            raise EmogiError(E_ARG, "one source per graph")
+        return s
+
+    def bfs(self, sources, out=None, **kw):
+        """emogi_batch_bfs -> (list of per-graph level arrays, stats dict)."""
+        s = self._srcs(sources)
+        if out is None:
+            buf = np.empty(max(self.total, 1), dtype=np.uint32)
+            ptr, on_dev = buf.ctypes.data, False
+        else:
+            buf, ptr, on_dev = out, out.data_ptr(), bool(out.is_cuda)
+        o = _opts(out_on_device=on_dev, **kw)
+        st = Stats()
+        _check(lib().emogi_batch_bfs(self._h, s.ctypes.data, ptr, ctypes.byref(o), ctypes.byref(st)))
+        views = [buf[o0:o0 + g.n] for o0, g in zip(self.offsets, self.graphs)]
+        return views, st.as_dict()
+
+    def autotune(self, sources):
+        """emogi_batch_autotune -> (granularity, claim, ms)."""
+        s = self._srcs(sources)
+        g, c, ms = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_double()
+        _check(lib().emogi_batch_autotune(self._h, s.ctypes.data, ctypes.byref(g), ctypes.byref(c),
+                                          ctypes.byref(ms)))
+        return int(g.value), int(c.value), float(ms.value)
+
+    def free(self):
+        if self._h:
+            lib().emogi_batch_free(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.free()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def bfs_batch(graphs, sources, **kw):
+    """emogi_bfs_batch (one-shot) -> (list of per-graph level arrays, stats dict)."""
+    graphs = list(graphs)
+    arr = (ctypes.c_void_p * len(graphs))(*[g.handle.value for g in graphs])
+    s = np.ascontiguousarray(np.asarray(sources, dtype=np.uint64).ravel())
+    total = sum(g.n for g in graphs)
+    buf = np.empty(max(total, 1), dtype=np.uint32)
+    o = _opts(**kw)
+    st = Stats()
+    _check(lib().emogi_bfs_batch(ctypes.cast(arr, ctypes.c_void_p), s.ctypes.data, buf.ctypes.data, len(graphs),
+                                 ctypes.byref(o), ctypes.byref(st)))
+    out, off = [], 0
+    for g in graphs:
+        out.append(buf[off:off + g.n])
+        off += g.n
+    return out, st.as_dict()
+
+
+QUERY_BFS, QUERY_SSSP = 0, 1
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("max_slots", ctypes.c_uint32),
+                ("device_budget", ctypes.c_uint64), ("max_batch", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+class QueryResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("batch_size", ctypes.c_uint32), ("queue_ms", ctypes.c_double),
+                ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
+                ("edges_reached", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class Server:
+    """emogi_server_*: continuous-batching query server over loaded graphs."""
+
+    def __init__(self, max_slots=4, device_budget=0, max_batch=0):
+        cfg = ServerConfig(ctypes.sizeof(ServerConfig), int(max_slots), int(device_budget), int(max_batch), 0)
+        h = ctypes.c_void_p()
+        _check(lib().emogi_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, graph: Graph, kind, src, out=None) -> int:
+        """Queue a query; `out` is a host uint32 array of n entries (or None)."""
+        k = {"bfs": QUERY_BFS, "sssp": QUERY_SSSP}.get(kind, kind)
+        ptr = None
+        if out is not None:
+            if out.dtype != np.uint32 or out.size < graph.n or not out.flags.c_contiguous:
+                raise EmogiError(E_ARG, "output array must be contiguous uint32 with n entries")
+            ptr = out.ctypes.data
+        t = ctypes.c_uint64()
+        _check(lib().emogi_server_submit(self._h, graph.handle, int(k), int(src), ptr, ctypes.byref(t)))
+        self._keep[t.value] = out
+        return int(t.value)
+
+    def wait(self, ticket, timeout_ns=0):
+        r = QueryResult()
+        st = lib().emogi_server_wait(self._h, int(ticket), int(timeout_ns), ctypes.byref(r))
+        if st != E_TIMEOUT:
+            self._keep.pop(int(ticket), None)
+        _check(st)
+        return r.as_dict()
+
+    def drain(self):
+        _check(lib().emogi_server_drain(self._h))
+
+    def device_bytes(self):
+        return int(lib().emogi_server_device_bytes(self._h))
+
+    def close(self):
+        if self._h:
+            lib().emogi_server_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

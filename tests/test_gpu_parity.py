@@ -114,6 +114,9 @@ def check_all(g, h, **kw):
     if g.undirected:
         lab, st = E.cc(h, **kw)
         np.testing.assert_array_equal(lab, oracle.cc_g(g), err_msg=f"cc {kw}")
+        assert st["edges_scanned"] <= g.m + 2 * g.n
+        lab, st = E.cc(h, cc_full_pass=True, **kw)
+        np.testing.assert_array_equal(lab, oracle.cc_g(g), err_msg=f"cc full pass {kw}")
         assert st["edges_scanned"] == g.m
 
 
@@ -282,14 +285,216 @@ def test_budget_and_injected_alloc_failure():
     assert E.device_bytes_in_use() == base
 
 
+@pytest.mark.parametrize("name", ["kron16", "urand14", "hub", "path", "kron12", "residues"])
+@pytest.mark.parametrize("kw", [dict(top_down_only=True), dict(), dict(granularity=4), dict(granularity=32)],
+                         ids=["top-down", "diropt", "diropt-g4", "diropt-g32"])
+def test_bfs_directions(name, kw):
+    """Direction-optimising BFS (bottom-up dense levels) gives the same levels as
+    the push-only form, and reads no more list entries than it."""
+    g = graph(name)
+    with E.load_graph(g, placement="host") as h:
+        for s in sources(g):
+            lv, st = E.bfs(h, s, **kw)
+            exp = oracle.bfs_g(g, s)
+            np.testing.assert_array_equal(lv, exp)
+            assert st["edges_reached"] == oracle.reached_edges(g.offsets, exp)
+            if kw.get("top_down_only"):
+                assert st["edges_scanned"] == st["edges_reached"]
+
+
+def test_direction_optimising_reads_less_on_dense_levels():
+    g = graph("kron16")
+    s = gg.max_degree_vertex(g)
+    with E.load_graph(g, placement="host") as h:
+        _, td = E.bfs(h, s, top_down_only=True)
+        _, do = E.bfs(h, s)
+        assert do["edges_scanned"] < 0.5 * td["edges_scanned"]
+
+
 def test_stats_are_consistent():
     g = graph("kron16")
     s = gg.max_degree_vertex(g)
     with E.load_graph(g, placement="host") as h:
-        lv, st = E.bfs(h, s, time_kernels=True)
+        lv, st = E.bfs(h, s, time_kernels=True, top_down_only=True)
         reached = oracle.reached_edges(g.offsets, lv)
         assert st["edges_scanned"] == reached  # BFS expands each reached vertex once
         assert st["edge_bytes"] == 8 * reached
         assert st["iterations"] == int(lv[lv != E.INF].max()) + 1
         assert st["expand_launches"] == st["iterations"]
         assert 0 < st["expand_ms"] <= st["ms"]
+
+
+# ------------------------------------------------------------------ multi-source BFS
+def ms_sources(g, k, seed=2):
+    srcs = [int(x) for x in gg.random_sources(g, k, seed=seed)]
+    while len(srcs) < k:  # small graphs: repeat sources (allowed)
+        srcs.append(srcs[len(srcs) % max(1, len(srcs))] if srcs else 0)
+    if k >= 3:
+        srcs[1] = srcs[0]  # a repeated source
+        srcs[2] = int(np.argmin(g.degrees()))  # possibly isolated
+    return srcs[:k]
+
+
+@pytest.mark.parametrize("placement", ["device", "host"])
+@pytest.mark.parametrize("k", [1, 5, 64])
+def test_msbfs_rows_equal_oracle_bfs(placement, k):
+    g = graph("kron16")
+    srcs = ms_sources(g, k)
+    with E.load_graph(g, placement=placement) as h:
+        lv, st = E.msbfs(h, srcs)
+        exp = oracle.msbfs(g.n, g.offsets, g.cols, srcs)
+        np.testing.assert_array_equal(lv, exp)
+        assert st["edges_reached"] == sum(oracle.reached_edges(g.offsets, exp[b]) for b in range(k))
+
+
+@pytest.mark.parametrize("name", ["hub", "path", "directed", "urand14", "residues", "single"])
+@pytest.mark.parametrize("variant", [dict(), dict(granularity=4), dict(granularity=32, chunk_lines=3),
+                                     dict(access="merged"), dict(access="naive")],
+                         ids=["auto", "g4", "g32-chunk3", "merged", "naive"])
+def test_msbfs_graph_set(name, variant):
+    g = graph(name)
+    k = 1 if g.n == 1 else 17
+    srcs = ms_sources(g, k)
+    with E.load_graph(g, placement="host") as h:
+        lv, _ = E.msbfs(h, srcs, **variant)
+        np.testing.assert_array_equal(lv, oracle.msbfs(g.n, g.offsets, g.cols, srcs))
+
+
+def test_msbfs_device_output_and_errors():
+    g = graph("kron12")
+    srcs = ms_sources(g, 9)
+    out = torch.empty((9, g.n), dtype=torch.int32, device="cuda")
+    with E.load_graph(g, placement="host") as h:
+        E.msbfs(h, srcs, out=out)
+        np.testing.assert_array_equal(out.cpu().numpy().view(np.uint32), oracle.msbfs(g.n, g.offsets, g.cols, srcs))
+        for bad in ([], list(range(65)), [g.n]):
+            with pytest.raises(E.EmogiError) as ei:
+                E.msbfs(h, bad)
+            assert ei.value.status == E.E_ARG
+
+
+# ------------------------------------------------------------------ batched BFS
+def uneven_graphs(count, seed=4, nmin=6, nmax=12):
+    """Uniform-random graphs of uneven sizes (2^nmin..2^nmax vertices, log-uniform)
+    and average degrees 4..64, plus a few degenerate members."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(2 ** rng.uniform(nmin, nmax))
+        d = int(rng.integers(4, 65))
+        out.append(gg.uniform(n, d, seed=seed * 1000 + i))
+    out.append(gg.path_graph(300))
+    out.append(hub_graph(5000))
+    out.append(gg.empty_graph(3))
+    return out
+
+
+@pytest.mark.parametrize("placement", ["device", "host"])
+def test_batch_bfs_equals_oracle(placement):
+    gs = uneven_graphs(40)
+    hs = [E.load_graph(g, placement=placement) for g in gs]
+    srcs = [gg.max_degree_vertex(g) for g in gs]
+    try:
+        with E.Batch(hs) as b:
+            for kw in (dict(), dict(granularity=4, chunk_lines=1), dict(granularity=32, chunk_lines=64)):
+                lv, st = b.bfs(srcs, **kw)
+                reached = 0
+                for g, h, s, got in zip(gs, hs, srcs, lv):
+                    exp = oracle.bfs_g(g, s)
+                    np.testing.assert_array_equal(got, exp)
+                    reached += oracle.reached_edges(g.offsets, exp)
+                assert st["edges_reached"] == reached
+            # the autotuner keeps a configuration that gives the same result
+            G, claim, ms = b.autotune(srcs)
+            assert G in (4, 8, 16, 32) and claim in (1, 4, 16, 64) and ms > 0
+            srcs2 = [int(gg.random_sources(g, 1, seed=9)[0]) if g.m else 0 for g in gs]
+            lv, _ = b.bfs(srcs2)
+            for g, s, got in zip(gs, srcs2, lv):
+                np.testing.assert_array_equal(got, oracle.bfs_g(g, s))
+            out = torch.empty(b.total, dtype=torch.int32, device="cuda")
+            lv, _ = b.bfs(srcs, out=out)
+            for g, s, got in zip(gs, srcs, lv):
+                np.testing.assert_array_equal(got.cpu().numpy().view(np.uint32), oracle.bfs_g(g, s))
+    finally:
+        for h in hs:
+            h.free()
+
+
+def test_bfs_batch_one_shot_and_errors():
+    gs = uneven_graphs(5, seed=8)
+    hs = [E.load_graph(g, placement="device") for g in gs]
+    try:
+        srcs = [0] * len(gs)
+        lv, _ = E.bfs_batch(hs, srcs)
+        for g, got in zip(gs, lv):
+            np.testing.assert_array_equal(got, oracle.bfs_g(g, 0))
+        with pytest.raises(E.EmogiError) as ei:
+            E.bfs_batch(hs, [g.n for g in gs])
+        assert ei.value.status == E.E_ARG
+        with pytest.raises(E.EmogiError) as ei:
+            E.bfs_batch(hs, srcs, access="naive")
+        assert ei.value.status == E.E_UNSUPPORTED
+    finally:
+        for h in hs:
+            h.free()
+
+
+def test_batch_barrier_timeout_is_reported_not_hung():
+    """A level barrier that waits longer than timeout_ns returns
+    EMOGI_E_TIMEOUT (the wait is bounded); a 1 ns bound trips it on the first
+    barrier while every block is co-resident, so nothing hangs."""
+    gs = uneven_graphs(8, seed=3)
+    hs = [E.load_graph(g, placement="device") for g in gs]
+    try:
+        with E.Batch(hs) as b:
+            with pytest.raises(E.EmogiError) as ei:
+                b.bfs([0] * len(gs), timeout_ns=1)
+            assert ei.value.status == E.E_TIMEOUT
+            lv, _ = b.bfs([0] * len(gs))  # the batch still works afterwards
+            for g, got in zip(gs, lv):
+                np.testing.assert_array_equal(got, oracle.bfs_g(g, 0))
+    finally:
+        for h in hs:
+            h.free()
+
+
+def many_components_graph():
+    """Several components of different sizes (a big uniform block, small
+    Kronecker blocks, paths, stars, isolated vertices) with ids interleaved by
+    a permutation, so that the sampled giant tree is not the only one."""
+    rng = np.random.default_rng(21)
+    parts, n = [], 0
+    for sub in [gg.uniform(3000, 6, seed=1), gg.kronecker(8, 4, seed=2), gg.path_graph(200),
+                gg.star_graph(50), gg.empty_graph(30), gg.uniform(500, 3, seed=3)]:
+        deg = np.diff(sub.offsets).astype(np.int64)
+        src = np.repeat(np.arange(sub.n), deg) + n
+        parts.append((src, sub.cols.astype(np.int64) + n))
+        n += sub.n
+    perm = rng.permutation(n)
+    s = perm[np.concatenate([p[0] for p in parts])]
+    d = perm[np.concatenate([p[1] for p in parts])]
+    return gg.csr_from_edges(n, s, d, symmetrize=True, name="many-components")
+
+
+@pytest.mark.parametrize("placement", ["device", "host"])
+@pytest.mark.parametrize("name", ["many", "kron16", "urand14", "hub", "path", "empty", "single", "residues-sym"])
+def test_cc_sampled_and_full_pass(placement, name):
+    if name == "many":
+        g = many_components_graph()
+    elif name == "residues-sym":
+        r = graph("residues")
+        deg = np.diff(r.offsets).astype(np.int64)
+        g = gg.csr_from_edges(r.n, np.repeat(np.arange(r.n), deg), r.cols, symmetrize=True, dedup=False,
+                              drop_self_loops=False)
+    else:
+        g = graph(name)
+    exp = oracle.cc_g(g)
+    with E.load_graph(g, placement=placement) as h:
+        for kw in (dict(), dict(cc_full_pass=True), dict(granularity=4), dict(granularity=32, chunk_lines=2)):
+            lab, st = E.cc(h, **kw)
+            np.testing.assert_array_equal(lab, exp, err_msg=str(kw))
+    if name in ("urand14", "kron16"):
+        with E.load_graph(g, placement=placement) as h:
+            _, full = E.cc(h, cc_full_pass=True)
+            _, smp = E.cc(h)
+            assert smp["edges_scanned"] < 0.5 * full["edges_scanned"]
