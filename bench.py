@@ -51,9 +51,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the multi-source, batched and serving measurements")
-    ap.add_argument("--ncu-case", action="store_true",
-                    help="profiling case: one BFS, SSSP and CC on a 2^22-vertex uniform graph (1.1 GB edges in "
-                         "pinned host memory), then exit")
+    ap.add_argument("--ncu-case", nargs="?", const="traversal", default=None,
+                    choices=["traversal", "msbfs", "batch"],
+                    help="profiling case, then exit: 'traversal' = one BFS, SSSP and CC on a 2^22-vertex uniform "
+                         "graph (1.1 GB edges in pinned host memory); 'msbfs' = one 64-source pass on a scale-22 "
+                         "Kronecker graph in host memory; 'batch' = one batched BFS over 128 uneven graphs in HBM")
     return ap.parse_args()
 
 
@@ -332,7 +334,8 @@ def ours(args):
 
     # ---- multi-source BFS, batched many-graph BFS and serving (rank 0)
     if rank == 0 and not args.no_extras:
-        for name, fn in (("msbfs", extra_msbfs), ("batch", extra_batch), ("serving", extra_serving)):
+        for name, fn in (("kron16_bfs", extra_kron16), ("msbfs", extra_msbfs), ("batch", extra_batch),
+                         ("serving", extra_serving)):
             try:
                 result[name] = fn(E, torch)
             except Exception as ex:  # noqa: BLE001 - report, keep the bench line
@@ -359,6 +362,28 @@ def _time(torch, fn, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1), (time.perf_counter() - t0) * 1e3, r
+
+
+def extra_kron16(E, torch):
+    """BFS from the highest-degree vertex of an undirected Kronecker graph
+    (scale 16, edge factor 16), from HBM and from pinned host memory: a
+    latency-bound case (about 2M edges)."""
+    import graphgen as gg
+    g = gg.kronecker(16, 16, seed=GEN_SEED)
+    src = gg.max_degree_vertex(g)
+    st = torch.cuda.Stream()
+    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    res = {"workload": f"Kronecker scale 16 ef 16 (n={g.n}, m={g.m}), source = max-degree vertex {src}"}
+    for place in ("device", "host"):
+        with E.load_graph(g, placement=place) as h:
+            for _ in range(3):
+                E.bfs(h, src, out=out, stream=st)
+            reps = 20
+            ms, _, stats = _time(torch, lambda: [E.bfs(h, src, out=out, stream=st)[1] for _ in range(reps)], st)
+            ms /= reps
+            res[place] = {"ms": round(ms, 4), "gteps": round(stats[-1]["edges_reached"] / (ms * 1e-3) / 1e9, 3),
+                          "levels": stats[-1]["iterations"]}
+    return res
 
 
 def extra_msbfs(E, torch):
@@ -568,12 +593,31 @@ def reference(args):
 
 
 def ncu_case(args):
-    """A small case for ncu captures: edges (1.1 GB) still far larger than L2,
-    a few hundred MB on the device, a few dozen launches."""
+    """Small cases for ncu captures: inputs still far larger than L2, a few
+    hundred MB to a few GB on the device, a few dozen launches."""
     import torch
     from paper_2006_06890_gb300 import _build
     _build.build()
     from paper_2006_06890_gb300 import emogi as E
+    import graphgen as gg
+    if args.ncu_case == "msbfs":
+        g = gg.kronecker(22, 16, seed=GEN_SEED)
+        srcs = [int(s) for s in gg.random_sources(g, 64, seed=SRC_SEED)]
+        out = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+        with E.load_graph(g, placement="host") as h:
+            st = E.msbfs(h, srcs, out=out)[1]
+        print(json.dumps({"ncu_case": "msbfs Kronecker scale 22 ef 16, 64 sources, host", "stats": st}))
+        return
+    if args.ncu_case == "batch":
+        rng = np.random.default_rng(4)
+        gs = [gg.uniform(int(2 ** rng.uniform(10, 18)), int(rng.integers(4, 65)), seed=4000 + i) for i in range(128)]
+        hs = [E.load_graph(g, placement="device") for g in gs]
+        with E.Batch(hs) as b:
+            st = b.bfs([gg.max_degree_vertex(g) for g in gs])[1]
+        for h in hs:
+            h.free()
+        print(json.dumps({"ncu_case": "batched BFS, 128 uneven uniform graphs, device", "stats": st}))
+        return
     g, srcs = make_graph(1 << 22, args.degree)
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
     with E.load_graph(g, placement="host") as h:

@@ -178,14 +178,18 @@ __device__ __forceinline__ void warp_atomic_min(uint32_t* out, uint32_t x) {
 // frontier empties, the far pile is split again with T raised past its
 // smallest distance.  Every vertex is expanded with its final distance, so
 // the fixed point is the exact shortest distance whatever the order.
-//   nflag / fflag: "queued in the near frontier / far pile" (one entry each);
+//   qround: the sweep a vertex is queued for.  An improvement in sweep r
+//     queues its vertex for sweep r + 1 unless an earlier improvement in the
+//     same sweep already did (atomicMax returns the previous stamp).  A vertex
+//     that is being expanded in sweep r and improved meanwhile is therefore
+//     always queued again, whichever distance its expansion read, and no
+//     ordering between the distance and the stamp is needed.
+//   fflag: "in the far pile" (the pile is only read by the split kernel);
 //   xd: the distance v was last expanded with, so a vertex queued twice
-//   (near and far) is not expanded twice with the same distance.
-// A vertex clears its near flag before it reads its distance, so an
-// improvement landing after the read queues it again.
+//     (near and far) is not expanded twice with the same distance.
 struct SsspOp {
     uint32_t* dist;
-    uint32_t* nflag;
+    uint32_t* qround;
     uint32_t* fflag;
     uint32_t* xd;
     uint32_t* far_q;
@@ -193,14 +197,13 @@ struct SsspOp {
     uint32_t* far_min;
     uint32_t* overflow;
     uint32_t T;
+    uint32_t round;
     uint32_t lmin;  // per-thread smallest distance sent to the far pile
     using S = uint32_t;
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = true;
     static constexpr bool kPush = true;
     __device__ __forceinline__ S begin(uint32_t v) {
-        atomicExch(nflag + v, 0u);
-        __threadfence();
         const uint32_t d = __ldcg(dist + v);
         if (d >= __ldcg(xd + v)) return INF;  // already expanded with this distance
         __stcg(xd + v, d);
@@ -220,8 +223,7 @@ struct SsspOp {
         if (nd >= *p) return false;
         const uint32_t old = atomicMin(p, nd);
         if (nd >= old) return false;
-        __threadfence();
-        if (nd < T) return atomicExch(nflag + u, 1u) == 0u;
+        if (nd < T) return atomicMax(qround + u, round + 1) < round + 1;
         lmin = nd < lmin ? nd : lmin;
         if (atomicExch(fflag + u, 1u) == 0u) push(far_q, far_count, u);
         return false;
@@ -401,7 +403,7 @@ __device__ __forceinline__ void visit_pair(const Sweep& c, Op& op, typename Op::
 
 // Steps whose loads a lane issues back to back before visiting them.
 #ifndef EMOGI_PIPELINE_STEPS
-#define EMOGI_PIPELINE_STEPS 4
+#define EMOGI_PIPELINE_STEPS 1
 #endif
 constexpr int kSteps = EMOGI_PIPELINE_STEPS;
 
@@ -602,13 +604,13 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
 }
 
 // SSSP far-pile split (the near frontier is empty): every pending far vertex
-// whose distance is below the new threshold T moves to the near frontier, the
-// others stay in the far pile; vertices already expanded with their current
-// distance are dropped.  Each vertex is in the pile once, and nothing else
-// runs meanwhile, so plain flag updates suffice.
+// whose distance is below the new threshold T moves to the near frontier of
+// sweep `round`, the others stay in the far pile; vertices already expanded
+// with their current distance are dropped.  Each vertex is in the pile once,
+// and nothing else runs meanwhile, so plain updates suffice.
 static __global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount_in, uint32_t* fq_out,
                             uint32_t* fcount_out, uint32_t* nq_out, uint32_t* ncount_out, const uint32_t* dist,
-                            uint32_t* nflag, uint32_t* fflag, const uint32_t* xd, uint32_t T,
+                            uint32_t* qround, uint32_t* fflag, const uint32_t* xd, uint32_t T, uint32_t round,
                             uint32_t* far_min) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
@@ -623,7 +625,7 @@ static __global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount
                 fflag[v] = 0u;
             } else if (d < T) {
                 fflag[v] = 0u;
-                nflag[v] = 1u;
+                qround[v] = round;  // queued for the next sweep
                 push(nq_out, ncount_out, v);
             } else {
                 lmin = d < lmin ? d : lmin;

@@ -301,16 +301,15 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
     DevCounters* ctr = ws.ctr;
     uint32_t* state = c.o.out_on_device ? dist : ws.state;
     const uint64_t n = g->n;
-    if (ws.flags_dirty) {
-        EMOGI_CUDA_TRY(cudaMemsetAsync(ws.flag, 0, n * 4, c.st));
-        EMOGI_CUDA_TRY(cudaMemsetAsync(ws.fflag, 0, n * 4, c.st));
-    }
+    if (ws.flags_dirty) EMOGI_CUDA_TRY(cudaMemsetAsync(ws.fflag, 0, n * 4, c.st));
     EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[0], c.st));
     EMOGI_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), c.st));
     EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->far_min, 0xFF, sizeof(uint32_t), c.st));
     EMOGI_CUDA_TRY(cudaMemsetAsync(ws.xd, 0xFF, n * 4, c.st));
+    uint32_t* qround = ws.flag;  // sweep stamps; all 0 = "queued for sweep 0" only matters for the source
+    EMOGI_CUDA_TRY(cudaMemsetAsync(qround, 0, n * 4, c.st));
     dev::k_init_single<<<grid_for(c, n), kThreads, 0, c.st>>>(state, (uint32_t)n, (uint32_t)src, ws.q[0],
-                                                               ws.flag, &ctr->qcount[0]);
+                                                               nullptr, &ctr->qcount[0]);
     EMOGI_CUDA_TRY(cudaGetLastError());
     c.kernel_launches++;
     ws.flags_dirty = true;
@@ -319,7 +318,14 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
     uint64_t T = std::min<uint64_t>(delta, dev::INF);
     int side = 0, fside = 0;
     uint64_t nk = 1, fk = 0;
-    uint32_t it = 0;
+    uint32_t it = 0, sweeps = 0;
+    // Window widths adapt to the work they carry: a window whose sweeps
+    // expanded few vertices (the first hops from the source, the long tail of
+    // far vertices) makes the next window wider, a heavy one narrower.  Small
+    // windows are rounds of almost no parallel work whose cost is latency;
+    // wider ones there re-expand only the few vertices they hold.
+    uint64_t widen = 1, window_work = 0;
+    const uint64_t light = n / 64 > 1024 ? n / 64 : 1024, heavy = n / 8 > 1 ? n / 8 : 1;
     while (nk > 0 || fk > 0) {
         // every sweep or split either expands a vertex with a smaller distance
         // than before or raises T; both are bounded
@@ -327,9 +333,11 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         if (nk > 0) {
             EMOGI_TRY(reset_sweep_counters(c, side));
             Sweep s = make_sweep(c, side, false);
-            dev::SsspOp op{state,          ws.flag,           ws.fflag,       ws.xd, ws.fq[fside],
-                           &ctr->fcount[fside], &ctr->far_min, &ctr->overflow, (uint32_t)T, dev::INF};
+            dev::SsspOp op{state,          qround,            ws.fflag,       ws.xd,       ws.fq[fside],
+                           &ctr->fcount[fside], &ctr->far_min, &ctr->overflow, (uint32_t)T, sweeps, dev::INF};
             EMOGI_TRY(sweep(c, s, op, nk));
+            sweeps++;
+            window_work += nk;
             EMOGI_TRY(read_counters(c));
             nk = ws.h_ctr->qcount[side ^ 1];
             fk = ws.h_ctr->fcount[fside];
@@ -337,7 +345,10 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         } else {
             // near frontier empty: raise T past the smallest pending far distance
             const uint64_t fmin = ws.h_ctr->far_min;
-            uint64_t Tn = fmin + delta;
+            if (window_work < light) widen = std::min<uint64_t>(widen * 2, 64);
+            else if (window_work > heavy) widen = std::max<uint64_t>(widen / 2, 1);
+            window_work = 0;
+            uint64_t Tn = fmin + delta * widen;
             if (Tn <= T) Tn = T + 1;
             T = std::min<uint64_t>(Tn, dev::INF);
             EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->qcount[side], 0, sizeof(uint32_t), c.st));
@@ -345,7 +356,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
             EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->far_min, 0xFF, sizeof(uint32_t), c.st));
             dev::k_far_split<<<grid_for(c, fk), kThreads, 0, c.st>>>(
                 ws.fq[fside], &ctr->fcount[fside], ws.fq[fside ^ 1], &ctr->fcount[fside ^ 1], ws.q[side],
-                &ctr->qcount[side], state, ws.flag, ws.fflag, ws.xd, (uint32_t)T, &ctr->far_min);
+                &ctr->qcount[side], state, qround, ws.fflag, ws.xd, (uint32_t)T, sweeps, &ctr->far_min);
             EMOGI_CUDA_TRY(cudaGetLastError());
             c.kernel_launches++;
             EMOGI_TRY(read_counters(c, false));
