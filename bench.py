@@ -493,7 +493,7 @@ def extra_serving(E, torch):
                                 "p50_ms": round(float(np.percentile(lat, 50)), 3),
                                 "p99_ms": round(float(np.percentile(lat, 99)), 3)}
         loads = []
-        with E.Server(max_slots=4) as srv:
+        with E.Server(max_slots=8) as srv:
             for rate in (1000, 5000, 20000):
                 qs = make_queries(2000)
                 gaps = rng.exponential(1.0 / rate, size=len(qs))

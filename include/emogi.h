@@ -82,9 +82,13 @@ enum {
     EMOGI_OPT_TOP_DOWN_ONLY = 1u << 1, /* BFS: expand every level from the frontier (push) as the paper
                                           does, never switch an undirected graph's dense levels to the
                                           bottom-up (pull) direction */
-    EMOGI_OPT_CC_FULL_PASS = 1u << 2   /* CC: stream the whole edge list as the paper does instead of
+    EMOGI_OPT_CC_FULL_PASS = 1u << 2,  /* CC: stream the whole edge list as the paper does instead of
                                           linking sampled neighbours first and skipping the vertices
                                           already in the largest sampled component */
+    EMOGI_OPT_HOST_LOOP = 1u << 3      /* SSSP: drive the sweep loop from the host (one counter
+                                          readback per sweep, as the paper's level loop) instead of a
+                                          recorded CUDA graph whose conditional loop decides on the
+                                          device */
 };
 
 /* Per-call options.  Pass NULL for defaults.  struct_size must be
@@ -94,7 +98,8 @@ typedef struct {
     uint32_t access;       /* emogi_access; default EMOGI_ACCESS_MERGED_ALIGNED */
     uint32_t granularity;  /* lanes per vertex for MERGED_ALIGNED: 4, 8, 16 or 32; 0 = automatic */
     uint32_t chunk_lines;  /* 128-byte lines per work item for split (long) lists; 0 = automatic */
-    uint64_t timeout_ns;   /* bound on device-side waits of persistent kernels; 0 = 2 s */
+    uint64_t timeout_ns;   /* bound on device-side waits of persistent kernels (0 = 2 s) and on
+                              the device-driven SSSP loop (0 = 60 s); EMOGI_E_TIMEOUT when passed */
     void* cuda_stream;     /* cudaStream_t to run on; NULL = the graph's own stream */
     int32_t out_on_device; /* 1: output pointers are device pointers of the current device */
     uint32_t flags;        /* EMOGI_OPT_* */

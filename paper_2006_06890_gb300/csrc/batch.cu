@@ -176,11 +176,16 @@ __global__ void __launch_bounds__(256) k_batch_bfs(BatchParams p) {
                             ok[0] = true;
                         }
                     }
+                    // read both neighbours' levels before either update
+                    uint32_t cur[2] = {0, 0};
+#pragma unroll
+                    for (int x = 0; x < 2; x++)
+                        if (ok[x]) cur[x] = lev[(uint32_t)u[x]];
 #pragma unroll
                     for (int x = 0; x < 2; x++) {
-                        if (ok[x]) {
+                        if (ok[x] && cur[x] == dev::INF) {
                             uint32_t* pl = lev + (uint32_t)u[x];
-                            if (*pl == dev::INF && atomicCAS(pl, dev::INF, L + 1) == dev::INF)
+                            if (atomicCAS(pl, dev::INF, L + 1) == dev::INF)
                                 push2(out_q, out_cnt, make_uint2(gi, (uint32_t)u[x]));
                         }
                     }

@@ -170,6 +170,9 @@ void release_workspace(emogi_graph g) {
     dev_free(ws.ms_front, ws.n * 8);
     dev_free(ws.ms_next, ws.n * 8);
     dev_free(ws.ms_out, ws.ms_out_bytes);
+    if (ws.sssp_exec) cudaGraphExecDestroy(ws.sssp_exec);
+    dev_free(ws.sssp_loop, 256);
+    if (ws.h_sssp_loop) cudaFreeHost(ws.h_sssp_loop);
     dev_free(ws.ctr, sizeof(DevCounters));
     // dev_free's accounting assumes the sizes it was allocated with; when a
     // partial allocation failed, unallocated entries are null and skipped.

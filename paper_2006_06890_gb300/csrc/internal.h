@@ -92,6 +92,12 @@ struct Workspace {
     unsigned long long* ms_next = nullptr;   // sources reaching v in the sweep under way
     uint32_t* ms_out = nullptr;              // k x n levels when the output is on the host
     size_t ms_out_bytes = 0;
+    // device-driven SSSP loop: its state block and its recorded CUDA graph
+    void* sssp_loop = nullptr;               // dev::SsspLoop in device memory
+    void* h_sssp_loop = nullptr;             // pinned staging copy
+    cudaGraphExec_t sssp_exec = nullptr;
+    uint32_t sssp_exec_G = 0;
+    uint32_t sssp_exec_chunk = 0;
 };
 
 }  // namespace emogi

@@ -152,10 +152,12 @@ struct BfsOp {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = true;
+    static constexpr bool kPeek = true;
     __device__ __forceinline__ S begin(uint32_t) { return 0; }
-    __device__ __forceinline__ bool visit(S, uint32_t, uint64_t u, uint32_t) {
+    __device__ __forceinline__ uint32_t peek(uint64_t u) const { return level[(uint32_t)u]; }
+    __device__ __forceinline__ bool visit(S, uint32_t, uint64_t u, uint32_t, uint32_t cur) {
         uint32_t* p = level + (uint32_t)u;
-        if (*p != INF) return false;
+        if (cur != INF) return false;
         if (atomicCAS(p, INF, next) != INF) return false;
         if (off) lf += off[(uint32_t)u + 1] - off[(uint32_t)u];
         return true;
@@ -211,7 +213,9 @@ struct SsspOp {
     }
     // A relaxation whose sum does not fit below INF is dropped and noted; the
     // host then checks whether some reachable vertex was left at INF.
-    __device__ __forceinline__ bool visit(uint32_t dv, uint32_t, uint64_t u64, uint32_t w) {
+    static constexpr bool kPeek = true;
+    __device__ __forceinline__ uint32_t peek(uint64_t u) const { return dist[(uint32_t)u]; }
+    __device__ __forceinline__ bool visit(uint32_t dv, uint32_t, uint64_t u64, uint32_t w, uint32_t cur) {
         const uint32_t u = (uint32_t)u64;
         const uint64_t nd64 = (uint64_t)dv + (uint64_t)w;
         if (nd64 >= (uint64_t)INF) {
@@ -220,7 +224,7 @@ struct SsspOp {
         }
         const uint32_t nd = (uint32_t)nd64;
         uint32_t* p = dist + u;
-        if (nd >= *p) return false;
+        if (nd >= cur) return false;  // cur may be stale, but only ever larger than the true value
         const uint32_t old = atomicMin(p, nd);
         if (nd >= old) return false;
         if (nd < T) return atomicMax(qround + u, round + 1) < round + 1;
@@ -256,7 +260,9 @@ struct MsBfsOp {
         if ((next[u] & nb) == nb) return false;  // a stale read only shows fewer bits
         return atomicOr(next + u, nb) == 0ull;
     }
-    __device__ __forceinline__ bool visit(S f, uint32_t, uint64_t u, uint32_t) { return visit_edge(f, u); }
+    static constexpr bool kPeek = false;
+    __device__ __forceinline__ uint32_t peek(uint64_t) const { return 0; }
+    __device__ __forceinline__ bool visit(S f, uint32_t, uint64_t u, uint32_t, uint32_t) { return visit_edge(f, u); }
     __device__ __forceinline__ void flush() {}
 };
 
@@ -283,8 +289,10 @@ struct CcOp {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = false;
+    static constexpr bool kPeek = false;
     __device__ __forceinline__ S begin(uint32_t) { return 0; }
-    __device__ __forceinline__ bool visit(S, uint32_t v, uint64_t u64, uint32_t) {
+    __device__ __forceinline__ uint32_t peek(uint64_t) const { return 0; }
+    __device__ __forceinline__ bool visit(S, uint32_t v, uint64_t u64, uint32_t, uint32_t) {
         uint32_t u = (uint32_t)u64;
         if (u >= v) return false;
         uint32_t a = v, b = u;
@@ -312,8 +320,10 @@ struct CcFinalOp {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = false;
+    static constexpr bool kPeek = false;
     __device__ __forceinline__ S begin(uint32_t v) { return __ldcg(parent + v) == giant ? kSkip : 0u; }
-    __device__ __forceinline__ bool visit(S, uint32_t v, uint64_t u64, uint32_t) {
+    __device__ __forceinline__ uint32_t peek(uint64_t) const { return 0; }
+    __device__ __forceinline__ bool visit(S, uint32_t v, uint64_t u64, uint32_t, uint32_t) {
         uint32_t a = v, b = (uint32_t)u64;
         for (;;) {
             a = uf_find(parent, a);
@@ -347,8 +357,10 @@ struct OverflowCheckOp {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = false;
+    static constexpr bool kPeek = false;
     __device__ __forceinline__ S begin(uint32_t v) { return __ldcg(dist + v); }
-    __device__ __forceinline__ bool visit(S dv, uint32_t, uint64_t u, uint32_t) {
+    __device__ __forceinline__ uint32_t peek(uint64_t) const { return 0; }
+    __device__ __forceinline__ bool visit(S dv, uint32_t, uint64_t u, uint32_t, uint32_t) {
         if (dv != INF && __ldcg(dist + (uint32_t)u) == INF) atomicExch(found, 1u);
         return false;
     }
@@ -391,10 +403,24 @@ __device__ __forceinline__ PairLoad load_pair(const Sweep& c, uint64_t j, uint64
     return p;
 }
 
+// The neighbours' current values (level, distance) a pair's updates compare
+// against, read before any update so that all of a lane's reads are in
+// flight together rather than one after another.
 template <class Op>
-__device__ __forceinline__ void visit_pair(const Sweep& c, Op& op, typename Op::S st, uint32_t v, const PairLoad& p) {
-    const bool p0 = (p.valid & 1u) && op.visit(st, v, p.id.x, p.w.x);
-    const bool p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y);
+__device__ __forceinline__ uint2 peek_pair(const Op& op, const PairLoad& p) {
+    uint2 cur = make_uint2(0, 0);
+    if (Op::kPeek) {
+        if (p.valid & 1u) cur.x = op.peek(p.id.x);
+        if (p.valid & 2u) cur.y = op.peek(p.id.y);
+    }
+    return cur;
+}
+
+template <class Op>
+__device__ __forceinline__ void visit_pair(const Sweep& c, Op& op, typename Op::S st, uint32_t v, const PairLoad& p,
+                                           uint2 cur) {
+    const bool p0 = (p.valid & 1u) && op.visit(st, v, p.id.x, p.w.x, cur.x);
+    const bool p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y, cur.y);
     if (Op::kPush) {
         if (p0) push(c.out_q, c.out_count, (uint32_t)p.id.x);
         if (p1) push(c.out_q, c.out_count, (uint32_t)p.id.y);
@@ -403,7 +429,7 @@ __device__ __forceinline__ void visit_pair(const Sweep& c, Op& op, typename Op::
 
 // Steps whose loads a lane issues back to back before visiting them.
 #ifndef EMOGI_PIPELINE_STEPS
-#define EMOGI_PIPELINE_STEPS 1
+#define EMOGI_PIPELINE_STEPS 4
 #endif
 constexpr int kSteps = EMOGI_PIPELINE_STEPS;
 
@@ -411,9 +437,8 @@ constexpr int kSteps = EMOGI_PIPELINE_STEPS;
 // Merged + aligned expansion with G lanes per vertex (G = 4, 8, 16, 32).
 // Loops are warp-uniform: a warp runs as many steps as its longest group.
 template <class Op, int G>
-__global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op_in) {
+__device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
     constexpr int GPW = 32 / G;
-    Op op = op_in;
     const uint32_t lane = threadIdx.x & 31u, glane = lane % G, grp = lane / G;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -444,23 +469,31 @@ __global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op_in) {
         const uint32_t maxsteps = __reduce_max_sync(0xffffffffu, steps);
         for (uint32_t t0 = 0; t0 < maxsteps; t0 += kSteps) {
             PairLoad p[kSteps];
+            uint2 cur[kSteps];
 #pragma unroll
             for (int u = 0; u < kSteps; u++)
                 p[u] = load_pair<Op>(c, a + (uint64_t)(t0 + u) * (2 * G) + 2 * glane, s, e, t0 + u < steps);
 #pragma unroll
-            for (int u = 0; u < kSteps; u++) visit_pair(c, op, st, v, p[u]);
+            for (int u = 0; u < kSteps; u++) cur[u] = peek_pair(op, p[u]);
+#pragma unroll
+            for (int u = 0; u < kSteps; u++) visit_pair(c, op, st, v, p[u], cur[u]);
         }
     }
     add_scanned(c, scanned);
     op.flush();
 }
 
+template <class Op, int G>
+__global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op_in) {
+    Op op = op_in;
+    expand_group_body<Op, G>(c, op);
+}
+
 // Split lists: work item i of vertex lq_v[slot] covers lines
 // [i * chunk_lines, (i + 1) * chunk_lines) of its aligned list; one warp per
 // item, 16 bytes per lane (four 128-byte lines per step).
 template <class Op>
-__global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op_in) {
-    Op op = op_in;
+__device__ __forceinline__ void expand_split_body(const Sweep& c, Op& op) {
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -483,13 +516,22 @@ __global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op_in) {
         const typename Op::S st = (typename Op::S)c.lq_state[lo];
         for (uint64_t j0 = cs; j0 < ce; j0 += 64 * kSteps) {
             PairLoad p[kSteps];
+            uint2 cur[kSteps];
 #pragma unroll
             for (int u = 0; u < kSteps; u++) p[u] = load_pair<Op>(c, j0 + 64 * u + 2 * lane, s, ce, true);
 #pragma unroll
-            for (int u = 0; u < kSteps; u++) visit_pair(c, op, st, v, p[u]);
+            for (int u = 0; u < kSteps; u++) cur[u] = peek_pair(op, p[u]);
+#pragma unroll
+            for (int u = 0; u < kSteps; u++) visit_pair(c, op, st, v, p[u], cur[u]);
         }
     }
     op.flush();
+}
+
+template <class Op>
+__global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op_in) {
+    Op op = op_in;
+    expand_split_body<Op>(c, op);
 }
 
 // Bottom-up BFS sweep (the pull direction of direction-optimising BFS, Beamer,
@@ -570,7 +612,8 @@ __global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op_in) {
         for (uint64_t i = s + lane; i < e; i += 32) {
             const uint64_t u = ld_edge(c.cols + i);
             const uint32_t w = Op::kWeights ? ld_w(c.w + i) : 0u;
-            if (op.visit(st, v, u, w) && Op::kPush) push(c.out_q, c.out_count, (uint32_t)u);
+            if (op.visit(st, v, u, w, Op::kPeek ? op.peek(u) : 0u) && Op::kPush)
+                push(c.out_q, c.out_count, (uint32_t)u);
         }
     }
     __syncwarp();
@@ -595,7 +638,8 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
         for (uint64_t i = s; i < e; i++) {
             const uint64_t u = ld_edge(c.cols + i);
             const uint32_t w = Op::kWeights ? ld_w(c.w + i) : 0u;
-            if (op.visit(st, v, u, w) && Op::kPush) push(c.out_q, c.out_count, (uint32_t)u);
+            if (op.visit(st, v, u, w, Op::kPeek ? op.peek(u) : 0u) && Op::kPush)
+                push(c.out_q, c.out_count, (uint32_t)u);
         }
     }
     __syncwarp();
@@ -608,10 +652,10 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
 // sweep `round`, the others stay in the far pile; vertices already expanded
 // with their current distance are dropped.  Each vertex is in the pile once,
 // and nothing else runs meanwhile, so plain updates suffice.
-static __global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount_in, uint32_t* fq_out,
-                            uint32_t* fcount_out, uint32_t* nq_out, uint32_t* ncount_out, const uint32_t* dist,
-                            uint32_t* qround, uint32_t* fflag, const uint32_t* xd, uint32_t T, uint32_t round,
-                            uint32_t* far_min) {
+__device__ __forceinline__ void far_split_body(const uint32_t* fq_in, const uint32_t* fcount_in, uint32_t* fq_out,
+                                               uint32_t* fcount_out, uint32_t* nq_out, uint32_t* ncount_out,
+                                               const uint32_t* dist, uint32_t* qround, uint32_t* fflag,
+                                               const uint32_t* xd, uint32_t T, uint32_t round, uint32_t* far_min) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t k = *fcount_in;
@@ -634,6 +678,137 @@ static __global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount
         }
     }
     warp_atomic_min(far_min, lmin);
+}
+
+static __global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount_in, uint32_t* fq_out,
+                                   uint32_t* fcount_out, uint32_t* nq_out, uint32_t* ncount_out, const uint32_t* dist,
+                                   uint32_t* qround, uint32_t* fflag, const uint32_t* xd, uint32_t T, uint32_t round,
+                                   uint32_t* far_min) {
+    far_split_body(fq_in, fcount_in, fq_out, fcount_out, nq_out, ncount_out, dist, qround, fflag, xd, T, round,
+                   far_min);
+}
+
+// ------------------------------------------------------------------ device-driven SSSP loop
+// The near/far SSSP loop with its decisions on the device: one iteration of a
+// CUDA graph's conditional while-node runs the sweep kernels, the far split
+// and a one-thread controller; the kernel that is not due this iteration
+// returns at once.  No host round trip separates iterations.
+struct SsspLoop {
+    uint32_t side;        // near frontier parity
+    uint32_t fside;       // far pile parity
+    uint32_t mode;        // 0 = sweep next, 1 = far split next, 2 = done
+    uint32_t T;           // current threshold
+    uint32_t sweeps;      // sweeps run (sweep stamp of the next sweep)
+    uint32_t iters;       // sweeps + splits run
+    uint32_t delta;       // base window width
+    uint32_t error;       // 1 = the iteration cap was reached, 2 = the time bound
+    unsigned long long cap;
+    unsigned long long t0, timeout_ns;  // %globaltimer at the first iteration; bound on the loop
+    unsigned long long widen, window_work, light, heavy;
+    uint32_t* dist;       // this call's distance array
+};
+
+// Fixed pointers of one graph's SSSP loop (recorded once in the CUDA graph).
+struct SsspFixed {
+    Sweep base;           // off, cols, w, shift, split-list queue, scanned
+    uint32_t* q[2];
+    uint32_t* fq[2];
+    uint32_t* qround;
+    uint32_t* fflag;
+    uint32_t* xd;
+};
+
+template <class Ctr>
+__device__ __forceinline__ void sssp_loop_views(const SsspFixed& f, const SsspLoop& L, Ctr* ctr, Sweep* s,
+                                                SsspOp* op) {
+    *s = f.base;
+    s->in_q = f.q[L.side];
+    s->in_count = &ctr->qcount[L.side];
+    s->out_q = f.q[L.side ^ 1];
+    s->out_count = &ctr->qcount[L.side ^ 1];
+    s->large = &ctr->large[0];
+    *op = SsspOp{L.dist, f.qround, f.fflag, f.xd, f.fq[L.fside], &ctr->fcount[L.fside], &ctr->far_min,
+                 &ctr->overflow, L.T, L.sweeps, INF};
+}
+
+template <class Ctr, int G>
+__global__ void __launch_bounds__(256) k_sssp_loop_sweep(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
+    const SsspLoop L = *Lp;
+    if (L.mode != 0) return;
+    Sweep s;
+    SsspOp op;
+    sssp_loop_views(f, L, ctr, &s, &op);
+    expand_group_body<SsspOp, G>(s, op);
+}
+
+template <class Ctr>
+__global__ void __launch_bounds__(256) k_sssp_loop_lists(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
+    const SsspLoop L = *Lp;
+    if (L.mode != 0) return;
+    Sweep s;
+    SsspOp op;
+    sssp_loop_views(f, L, ctr, &s, &op);
+    expand_split_body<SsspOp>(s, op);
+}
+
+template <class Ctr>
+__global__ void __launch_bounds__(256) k_sssp_loop_far(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
+    const SsspLoop L = *Lp;
+    if (L.mode != 1) return;
+    far_split_body(f.fq[L.fside], &ctr->fcount[L.fside], f.fq[L.fside ^ 1], &ctr->fcount[L.fside ^ 1],
+                   f.q[L.side], &ctr->qcount[L.side], L.dist, f.qround, f.fflag, f.xd, L.T, L.sweeps, &ctr->far_min);
+}
+
+// One thread: account for the iteration that just ran, pick the next one
+// (sweep while the near frontier is non-empty, else split the far pile with
+// a raised threshold, else stop), clear the counters it will fill, and set
+// the loop condition.
+template <class Ctr>
+__global__ void k_sssp_loop_control(SsspLoop* Lp, Ctr* ctr, cudaGraphConditionalHandle handle) {
+    SsspLoop L = *Lp;
+    uint64_t nk = 0, fk = 0;
+    if (L.mode == 0) {
+        L.window_work += ctr->qcount[L.side];
+        nk = ctr->qcount[L.side ^ 1];
+        fk = ctr->fcount[L.fside];
+        L.side ^= 1;
+        L.sweeps++;
+    } else {
+        L.fside ^= 1;
+        nk = ctr->qcount[L.side];
+        fk = ctr->fcount[L.fside];
+    }
+    L.iters++;
+    unsigned long long now;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(now));
+    if (L.t0 == 0) L.t0 = now;
+    if (L.iters > L.cap) {
+        L.error = 1;
+        L.mode = 2;
+    } else if (now - L.t0 > L.timeout_ns) {
+        L.error = 2;
+        L.mode = 2;
+    } else if (nk > 0) {
+        L.mode = 0;
+        ctr->qcount[L.side ^ 1] = 0;
+        ctr->large[0] = 0;
+    } else if (fk > 0) {
+        L.mode = 1;
+        if (L.light && L.window_work < L.light) L.widen = L.widen * 2 < 16 ? L.widen * 2 : 16;
+        else if (L.window_work > L.heavy) L.widen = L.widen / 2 > 1 ? L.widen / 2 : 1;
+        L.window_work = 0;
+        uint64_t Tn = (uint64_t)ctr->far_min + (uint64_t)L.delta * L.widen;
+        if (Tn <= L.T) Tn = (uint64_t)L.T + 1;
+        L.T = Tn < (uint64_t)INF ? (uint32_t)Tn : INF;
+        ctr->qcount[L.side] = 0;
+        ctr->fcount[L.fside ^ 1] = 0;
+        ctr->far_min = INF;
+    } else {
+        L.mode = 2;
+    }
+    *Lp = L;
+    __threadfence();
+    cudaGraphSetConditional(handle, L.mode != 2 ? 1u : 0u);
 }
 
 // ------------------------------------------------------------------ small kernels

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -15,7 +17,24 @@ namespace {
 using dev::Sweep;
 
 constexpr int kThreads = 256;
+
+// SSSP windows that expanded fewer than n >> EMOGI_SSSP_LIGHT_SHIFT vertices
+// make the next window wider (0 = fixed windows).
+#ifndef EMOGI_SSSP_LIGHT_SHIFT
+#define EMOGI_SSSP_LIGHT_SHIFT 16
+#endif
 constexpr uint32_t kLargeLines = 32;  // lists above 32 lines (4 KiB) are split
+
+// EMOGI_TRACE=1 in the environment prints one line per sweep to stderr
+// (algorithm, sweep, frontier size, event-timed duration).  It forces the
+// per-sweep events on, so it is for diagnosis, not for timed runs.
+bool trace_enabled() {
+    static const bool on = [] {
+        const char* e = getenv("EMOGI_TRACE");
+        return e && *e && *e != '0';
+    }();
+    return on;
+}
 
 struct Ctx {
     emogi_graph g;
@@ -60,6 +79,7 @@ emogi_status setup(emogi_graph g, const emogi_opts* opts, Ctx* c) {
     c->G = c->o.granularity ? c->o.granularity : auto_granularity(g->avg_degree);
     c->chunk = c->o.chunk_lines ? c->o.chunk_lines : 32;
     c->sms = sm_count(g->device);
+    if (trace_enabled()) c->o.flags |= EMOGI_OPT_TIME_KERNELS;
     return EMOGI_OK;
 }
 
@@ -154,6 +174,11 @@ emogi_status read_counters(Ctx& c, bool after_sweep = true) {
         float ms = 0.f;
         EMOGI_CUDA_TRY(cudaEventElapsedTime(&ms, ws.ev[2], ws.ev[3]));
         c.expand_ms += ms;
+        if (trace_enabled())
+            fprintf(stderr, "[emogi] sweep %llu in=%u/%u out=%u/%u far=%u/%u scanned=%llu ms=%.4f\n",
+                    (unsigned long long)c.expand_launches, ws.h_ctr->qcount[0], ws.h_ctr->qcount[1],
+                    ws.h_ctr->qcount[1], ws.h_ctr->qcount[0], ws.h_ctr->fcount[0], ws.h_ctr->fcount[1],
+                    (unsigned long long)ws.h_ctr->scanned, ms);
     }
     return EMOGI_OK;
 }
@@ -230,6 +255,70 @@ emogi_status check_output(emogi_graph g, const Opts& o, void* out) {
             return fail(EMOGI_E_ARG, "out_on_device is set but the output is not device memory");
         }
     }
+    return EMOGI_OK;
+}
+
+// Records the device-driven SSSP loop of graph g as a CUDA graph (once per
+// granularity / chunk choice): a conditional while-node whose body runs the
+// sweep kernels, the far split and the controller.
+emogi_status build_sssp_exec(Ctx& c) {
+    emogi_graph g = c.g;
+    Workspace& ws = g->ws;
+    if (ws.sssp_exec && ws.sssp_exec_G == c.G && ws.sssp_exec_chunk == c.chunk) return EMOGI_OK;
+    if (ws.sssp_exec) {
+        cudaGraphExecDestroy(ws.sssp_exec);
+        ws.sssp_exec = nullptr;
+    }
+    dev::SsspFixed f;
+    f.base = make_sweep(c, 0, false);
+    f.q[0] = ws.q[0];
+    f.q[1] = ws.q[1];
+    f.fq[0] = ws.fq[0];
+    f.fq[1] = ws.fq[1];
+    f.qround = ws.flag;
+    f.fflag = ws.fflag;
+    f.xd = ws.xd;
+    dev::SsspLoop* L = (dev::SsspLoop*)ws.sssp_loop;
+    cudaGraph_t graph = nullptr;
+    EMOGI_CUDA_TRY(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = handle;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(EMOGI_E_CUDA, "SSSP loop graph: %s", cudaGetErrorString(e));
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    cudaStream_t cs = g->stream;  // record on the graph's own (non-default) stream
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const int big = c.sms * 8, lists = c.sms * 4;
+        switch (c.G) {
+            case 4: dev::k_sssp_loop_sweep<DevCounters, 4><<<big, kThreads, 0, cs>>>(f, L, ws.ctr); break;
+            case 8: dev::k_sssp_loop_sweep<DevCounters, 8><<<big, kThreads, 0, cs>>>(f, L, ws.ctr); break;
+            case 16: dev::k_sssp_loop_sweep<DevCounters, 16><<<big, kThreads, 0, cs>>>(f, L, ws.ctr); break;
+            default: dev::k_sssp_loop_sweep<DevCounters, 32><<<big, kThreads, 0, cs>>>(f, L, ws.ctr); break;
+        }
+        dev::k_sssp_loop_lists<DevCounters><<<lists, kThreads, 0, cs>>>(f, L, ws.ctr);
+        dev::k_sssp_loop_far<DevCounters><<<big, kThreads, 0, cs>>>(f, L, ws.ctr);
+        dev::k_sssp_loop_control<DevCounters><<<1, 1, 0, cs>>>(L, ws.ctr, handle);
+        cudaGraph_t captured = body;
+        e = cudaStreamEndCapture(cs, &captured);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ws.sssp_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        ws.sssp_exec = nullptr;
+        return fail(EMOGI_E_CUDA, "recording the SSSP loop: %s", cudaGetErrorString(e));
+    }
+    ws.sssp_exec_G = c.G;
+    ws.sssp_exec_chunk = c.chunk;
     return EMOGI_OK;
 }
 
@@ -315,17 +404,55 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
     ws.flags_dirty = true;
 
     const uint64_t delta = c.o.delta ? c.o.delta : auto_delta(g);
+    uint32_t it = 0, sweeps = 0;
+    const bool device_loop = c.o.access == EMOGI_ACCESS_MERGED_ALIGNED && !(c.o.flags & EMOGI_OPT_HOST_LOOP);
+    if (device_loop) {
+        if (!ws.sssp_loop) {
+            EMOGI_TRY(dev_alloc(&ws.sssp_loop, 256, "SSSP loop state"));
+            EMOGI_CUDA_TRY(cudaHostAlloc(&ws.h_sssp_loop, 256, cudaHostAllocDefault));
+        }
+        EMOGI_TRY(build_sssp_exec(c));
+        dev::SsspLoop* hl = (dev::SsspLoop*)ws.h_sssp_loop;
+        memset(hl, 0, sizeof *hl);
+        hl->T = (uint32_t)std::min<uint64_t>(delta, dev::INF);
+        hl->delta = (uint32_t)std::min<uint64_t>(delta, dev::INF);
+        hl->cap = 4 * n + 8;
+        hl->widen = 1;
+        hl->light = EMOGI_SSSP_LIGHT_SHIFT ? std::max<uint64_t>(n >> EMOGI_SSSP_LIGHT_SHIFT, 256) : 0;
+        hl->heavy = std::max<uint64_t>(n >> 6, 1);
+        hl->dist = state;
+        // the loop runs on the device: bound it in time as well (the caller's
+        // timeout_ns when given, else one minute)
+        hl->timeout_ns = (opts && opts->timeout_ns) ? opts->timeout_ns : 60000000000ull;
+        EMOGI_CUDA_TRY(cudaMemcpyAsync(ws.sssp_loop, hl, sizeof *hl, cudaMemcpyHostToDevice, c.st));
+        const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
+        if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
+        EMOGI_CUDA_TRY(cudaGraphLaunch(ws.sssp_exec, c.st));
+        if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[3], c.st));
+        EMOGI_CUDA_TRY(cudaMemcpyAsync(hl, ws.sssp_loop, sizeof *hl, cudaMemcpyDeviceToHost, c.st));
+        EMOGI_TRY(read_counters(c));
+        if (hl->error == 1) return fail(EMOGI_E_TIMEOUT, "SSSP did not converge in %u rounds", hl->iters);
+        if (hl->error)
+            return fail(EMOGI_E_TIMEOUT, "SSSP loop passed its time bound of %llu ns after %u rounds",
+                        (unsigned long long)hl->timeout_ns, hl->iters);
+        it = hl->iters;
+        sweeps = hl->sweeps;
+        c.expand_launches += sweeps;
+        c.kernel_launches += 4ull * it;
+    }
     uint64_t T = std::min<uint64_t>(delta, dev::INF);
     int side = 0, fside = 0;
-    uint64_t nk = 1, fk = 0;
-    uint32_t it = 0, sweeps = 0;
+    uint64_t nk = device_loop ? 0 : 1, fk = 0;
     // Window widths adapt to the work they carry: a window whose sweeps
-    // expanded few vertices (the first hops from the source, the long tail of
-    // far vertices) makes the next window wider, a heavy one narrower.  Small
-    // windows are rounds of almost no parallel work whose cost is latency;
-    // wider ones there re-expand only the few vertices they hold.
+    // expanded very few vertices (under n/65536: the first hops from the
+    // source, the long tail of far vertices) makes the next window twice as
+    // wide (up to 16x), a heavy one (over n/64) halves it again.  Tiny windows
+    // are rounds of almost no parallel work whose cost is latency; wider ones
+    // there re-expand only the few vertices they hold.  (A threshold of n/64
+    // measured worse on a uniform degree-32 graph: 1.64x re-expansion.)
     uint64_t widen = 1, window_work = 0;
-    const uint64_t light = n / 64 > 1024 ? n / 64 : 1024, heavy = n / 8 > 1 ? n / 8 : 1;
+    const uint64_t light = EMOGI_SSSP_LIGHT_SHIFT ? std::max<uint64_t>(n >> EMOGI_SSSP_LIGHT_SHIFT, 256) : 0;
+    const uint64_t heavy = std::max<uint64_t>(n >> 6, 1);
     while (nk > 0 || fk > 0) {
         // every sweep or split either expands a vertex with a smaller distance
         // than before or raises T; both are bounded
@@ -345,7 +472,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         } else {
             // near frontier empty: raise T past the smallest pending far distance
             const uint64_t fmin = ws.h_ctr->far_min;
-            if (window_work < light) widen = std::min<uint64_t>(widen * 2, 64);
+            if (window_work < light) widen = std::min<uint64_t>(widen * 2, 16);
             else if (window_work > heavy) widen = std::max<uint64_t>(widen / 2, 1);
             window_work = 0;
             uint64_t Tn = fmin + delta * widen;

@@ -202,6 +202,33 @@ def test_sssp_windows(name, delta):
             np.testing.assert_array_equal(d, oracle.sssp_g(g, s), err_msg=f"sssp src={s} delta={delta}")
 
 
+@pytest.mark.parametrize("name", ["kron16", "urand14", "hub", "path", "directed"])
+def test_sssp_device_loop_equals_host_loop(name):
+    """The device-driven SSSP loop (recorded CUDA graph with a conditional
+    while-node) and the host-driven loop give the oracle's distances."""
+    g = graph(name)
+    with E.load_graph(g, placement="host") as h:
+        for s in sources(g):
+            exp = oracle.sssp_g(g, s)
+            d1, st1 = E.sssp(h, s)
+            d2, st2 = E.sssp(h, s, host_loop=True)
+            np.testing.assert_array_equal(d1, exp)
+            np.testing.assert_array_equal(d2, exp)
+            for G in (4, 32):  # a different granularity records a new loop graph
+                np.testing.assert_array_equal(E.sssp(h, s, granularity=G)[0], exp)
+
+
+def test_sssp_device_loop_time_bound():
+    """The device loop checks %globaltimer at every iteration; a 1 ns bound
+    stops it with EMOGI_E_TIMEOUT, and the next call is exact again."""
+    g = graph("path")
+    with E.load_graph(g, placement="device") as h:
+        with pytest.raises(E.EmogiError) as ei:
+            E.sssp(h, 0, timeout_ns=1)
+        assert ei.value.status == E.E_TIMEOUT
+        np.testing.assert_array_equal(E.sssp(h, 0)[0], oracle.sssp_g(g, 0))
+
+
 def test_sssp_zero_and_extreme_weights():
     rng = np.random.default_rng(4)
     n, m = 2000, 12000
