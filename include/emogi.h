@@ -60,7 +60,10 @@ typedef enum {
 /* emogi_load_csr flags */
 enum {
     EMOGI_LOAD_UNDIRECTED = 1u << 0, /* caller asserts the CSR is symmetric; required by emogi_cc */
-    EMOGI_LOAD_BORROW = 1u << 1      /* HOST only: pin and map the caller's arrays in place, no copy */
+    EMOGI_LOAD_BORROW = 1u << 1,     /* HOST only: pin and map the caller's arrays in place, no copy */
+    EMOGI_LOAD_NO_HEADS = 1u << 2    /* HOST / MANAGED: do not mirror the first 4 ids of every list in
+                                        GPU memory (16 bytes per vertex; sampled CC and bottom-up BFS
+                                        read them there instead of over the host link) */
 };
 
 /* How a worker reads one neighbour list (Sec. 4.2, Sec. 4.3, Listings

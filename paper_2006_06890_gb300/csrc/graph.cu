@@ -126,8 +126,6 @@ emogi_status ensure_workspace(emogi_graph g) {
         {(void**)&ws.state, n * 4, "vertex state"},
         {(void**)&ws.flag, n * 4, "near flags"},
         {(void**)&ws.fflag, n * 4, "far flags"},
-        {(void**)&ws.fq[0], n * 4, "far pile 0"},
-        {(void**)&ws.fq[1], n * 4, "far pile 1"},
         {(void**)&ws.xd, n * 4, "expanded distances"},
         {(void**)&ws.lq_v, ws.lq_cap * 4, "split-list vertices"},
         {(void**)&ws.lq_base, ws.lq_cap * 8, "split-list chunk bases"},
@@ -160,8 +158,6 @@ void release_workspace(emogi_graph g) {
     dev_free(ws.state, ws.n * 4);
     dev_free(ws.flag, ws.n * 4);
     dev_free(ws.fflag, ws.n * 4);
-    dev_free(ws.fq[0], ws.n * 4);
-    dev_free(ws.fq[1], ws.n * 4);
     dev_free(ws.xd, ws.n * 4);
     dev_free(ws.lq_v, ws.lq_cap * 4);
     dev_free(ws.lq_base, ws.lq_cap * 8);
@@ -308,6 +304,33 @@ static emogi_status place_array(int place, bool borrow, int device, const void* 
     return EMOGI_OK;
 }
 
+// heads[v * 4 + r] = col_idx[row_offsets[v] + r] for r < degree, else
+// UINT32_MAX; gathered on the host from the caller's arrays (no device read
+// of the placed edge list, so a managed edge list is not migrated by this).
+static emogi_status build_heads(emogi_graph g, const uint64_t* off, const uint64_t* cols) {
+    const uint64_t n = g->n;
+    std::vector<uint32_t> h;
+    try {
+        h.resize(n * 4);
+    } catch (...) {
+        return fail(EMOGI_E_NOMEM, "list heads staging (%llu bytes)", (unsigned long long)(n * 16));
+    }
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n < 65536) nt = 1;
+    auto work = [&](unsigned t) {
+        const uint64_t v0 = n * t / nt, v1 = n * (t + 1) / nt;
+        for (uint64_t v = v0; v < v1; v++)
+            for (uint64_t r = 0; r < 4; r++)
+                h[v * 4 + r] = off[v] + r < off[v + 1] ? (uint32_t)cols[off[v] + r] : 0xFFFFFFFFu;
+    };
+    std::vector<std::thread> th;
+    for (unsigned t = 1; t < nt; t++) th.emplace_back(work, t);
+    work(0);
+    for (auto& x : th) x.join();
+    EMOGI_CUDA_TRY(cudaMemcpy(g->d_heads, h.data(), n * 16, cudaMemcpyHostToDevice));
+    return EMOGI_OK;
+}
+
 static void release_array(int place, void* owned, const void* borrowed, size_t bytes) {
     size_t alloc = ((bytes + 127) / 128) * 128 + 128;
     if (borrowed) cudaHostUnregister((void*)borrowed);
@@ -360,7 +383,7 @@ emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets,
     if (m && !col_idx) return fail(EMOGI_E_ARG, "col_idx is NULL");
     if ((int)place < EMOGI_PLACE_DEVICE || (int)place > EMOGI_PLACE_MANAGED)
         return fail(EMOGI_E_ARG, "unknown placement %d", (int)place);
-    if (flags & ~(uint32_t)(EMOGI_LOAD_UNDIRECTED | EMOGI_LOAD_BORROW))
+    if (flags & ~(uint32_t)(EMOGI_LOAD_UNDIRECTED | EMOGI_LOAD_BORROW | EMOGI_LOAD_NO_HEADS))
         return fail(EMOGI_E_ARG, "unknown load flags 0x%x", flags);
     const bool borrow = flags & EMOGI_LOAD_BORROW;
     if (borrow && place != EMOGI_PLACE_HOST) return fail(EMOGI_E_ARG, "EMOGI_LOAD_BORROW needs EMOGI_PLACE_HOST");
@@ -409,6 +432,15 @@ emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets,
         if (s != EMOGI_OK) return bail(s);
         g->w = (const uint32_t*)kp;
     }
+    // list heads: the first ids of every list mirrored in GPU memory when the
+    // edge list itself is not there (16 bytes per vertex)
+    if (place != EMOGI_PLACE_DEVICE && !(flags & EMOGI_LOAD_NO_HEADS) && n && m) {
+        s = dev_alloc((void**)&g->d_heads, n * 4 * sizeof(uint32_t), "list heads");
+        if (s != EMOGI_OK) return bail(s);
+        g->dev_bytes += n * 4 * sizeof(uint32_t);
+        s = build_heads(g, row_offsets, col_idx);
+        if (s != EMOGI_OK) return bail(s);
+    }
     *out = g;
     return EMOGI_OK;
 }
@@ -419,6 +451,7 @@ emogi_status emogi_free_graph(emogi_graph g) {
     if (g->stream) cudaStreamSynchronize(g->stream);
     release_workspace(g);
     if (!g->shared) {
+        if (g->d_heads) dev_free(g->d_heads, g->n * 4 * sizeof(uint32_t));
         release_array(g->place, g->cols_owned, g->cols_borrowed, g->m * sizeof(uint64_t));
         if (g->w || g->w_owned || g->w_borrowed)
             release_array(g->place, g->w_owned, g->w_borrowed, g->m * sizeof(uint32_t));
@@ -443,6 +476,7 @@ emogi_status emogi_graph_share(emogi_graph g, emogi_graph* out) {
     h->flags = g->flags;
     h->place = g->place;
     h->d_off = g->d_off;
+    h->d_heads = g->d_heads;
     h->cols = g->cols;
     h->w = g->w;
     h->shift = g->shift;

@@ -56,7 +56,7 @@ emogi_status parse_opts(const emogi_opts* in, Opts* out);
 // memset clears them.
 struct DevCounters {
     uint32_t qcount[2];              // frontier sizes (ping-pong)
-    uint32_t fcount[2];              // SSSP far-pile sizes (ping-pong)
+    uint32_t fcount[2];              // SSSP: [0] = far vertices kept by the last split
     uint32_t far_min;                // SSSP: smallest distance sent to the far pile
     uint32_t overflow;               // SSSP: a distance reached UINT32_MAX
     uint32_t error;                  // device-side error code (bounded waits)
@@ -74,8 +74,7 @@ struct Workspace {
     uint32_t* q[2] = {nullptr, nullptr};   // frontier queues, n entries each
     uint32_t* state = nullptr;             // level / dist / parent when output is on the host
     uint32_t* flag = nullptr;              // SSSP "in near frontier" flags, all zero between calls
-    uint32_t* fflag = nullptr;             // SSSP "in far pile" flags, all zero between calls
-    uint32_t* fq[2] = {nullptr, nullptr};  // SSSP far piles
+    uint32_t* fflag = nullptr;             // SSSP "in the far pile" flags, all zero between calls
     uint32_t* xd = nullptr;                // SSSP distance of the last expansion
     bool flags_dirty = false;              // a call ended early and left flags set
     uint32_t* lq_v = nullptr;              // split-list vertices
@@ -108,6 +107,7 @@ struct emogi_graph_s {
     uint32_t flags = 0;
     int place = EMOGI_PLACE_DEVICE;
     uint64_t* d_off = nullptr;         // device row offsets (n + 1)
+    uint32_t* d_heads = nullptr;       // first 4 ids of every list in GPU memory (edge lists off the GPU)
     const uint64_t* cols = nullptr;    // kernel-visible edge list
     const uint32_t* w = nullptr;       // kernel-visible weights or null
     void* cols_owned = nullptr;        // what to free (device / pinned / managed)

@@ -53,7 +53,11 @@ struct Sweep {
     uint32_t large_lines = 0xFFFFFFFFu;  // lists with more lines than this are split
     uint32_t chunk_lines = 1;            // lines per split work item
     unsigned long long* scanned = nullptr;         // neighbour entries read (statistics)
+    const uint32_t* heads = nullptr;     // first kHeads ids of every list in GPU memory, or null
 };
+
+// Entries of each list mirrored in GPU memory ("list heads", INF-padded).
+constexpr int kHeads = 4;
 
 // ------------------------------------------------------------------ loads
 // Edge-list reads go through the non-coherent read-only path and do not
@@ -152,6 +156,7 @@ struct BfsOp {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = true;
+    static constexpr int kSteps = 4;
     static constexpr bool kPeek = true;
     __device__ __forceinline__ S begin(uint32_t) { return 0; }
     __device__ __forceinline__ uint32_t peek(uint64_t u) const { return level[(uint32_t)u]; }
@@ -186,7 +191,10 @@ __device__ __forceinline__ void warp_atomic_min(uint32_t* out, uint32_t x) {
 //     that is being expanded in sweep r and improved meanwhile is therefore
 //     always queued again, whichever distance its expansion read, and no
 //     ordering between the distance and the stamp is needed.
-//   fflag: "in the far pile" (the pile is only read by the split kernel);
+//   fflag: "in the far pile".  The pile is a flag per vertex, set with a
+//     plain store; the split kernel scans all flags.  (A queue needed an
+//     atomic exchange plus an append on one shared counter per vertex sent
+//     to the pile.)
 //   xd: the distance v was last expanded with, so a vertex queued twice
 //     (near and far) is not expanded twice with the same distance.
 struct SsspOp {
@@ -194,8 +202,6 @@ struct SsspOp {
     uint32_t* qround;
     uint32_t* fflag;
     uint32_t* xd;
-    uint32_t* far_q;
-    uint32_t* far_count;
     uint32_t* far_min;
     uint32_t* overflow;
     uint32_t T;
@@ -205,6 +211,7 @@ struct SsspOp {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = true;
     static constexpr bool kPush = true;
+    static constexpr int kSteps = 1;
     __device__ __forceinline__ S begin(uint32_t v) {
         const uint32_t d = __ldcg(dist + v);
         if (d >= __ldcg(xd + v)) return INF;  // already expanded with this distance
@@ -229,7 +236,7 @@ struct SsspOp {
         if (nd >= old) return false;
         if (nd < T) return atomicMax(qround + u, round + 1) < round + 1;
         lmin = nd < lmin ? nd : lmin;
-        if (atomicExch(fflag + u, 1u) == 0u) push(far_q, far_count, u);
+        fflag[u] = 1u;  // idempotent: the split scans the flags, no queue to append to
         return false;
     }
     __device__ __forceinline__ void flush() { warp_atomic_min(far_min, lmin); }
@@ -248,6 +255,7 @@ struct MsBfsOp {
     static constexpr S kSkip = 0ull;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = true;
+    static constexpr int kSteps = 1;
     __device__ __forceinline__ S begin(uint32_t v) {
         const S f = front[v];
         if (f) front[v] = 0ull;  // each vertex is queued once per sweep
@@ -289,6 +297,7 @@ struct CcOp {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = false;
+    static constexpr int kSteps = 1;
     static constexpr bool kPeek = false;
     __device__ __forceinline__ S begin(uint32_t) { return 0; }
     __device__ __forceinline__ uint32_t peek(uint64_t) const { return 0; }
@@ -320,6 +329,7 @@ struct CcFinalOp {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = false;
+    static constexpr int kSteps = 1;
     static constexpr bool kPeek = false;
     __device__ __forceinline__ S begin(uint32_t v) { return __ldcg(parent + v) == giant ? kSkip : 0u; }
     __device__ __forceinline__ uint32_t peek(uint64_t) const { return 0; }
@@ -357,6 +367,7 @@ struct OverflowCheckOp {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = false;
+    static constexpr int kSteps = 1;
     static constexpr bool kPeek = false;
     __device__ __forceinline__ S begin(uint32_t v) { return __ldcg(dist + v); }
     __device__ __forceinline__ uint32_t peek(uint64_t) const { return 0; }
@@ -427,11 +438,11 @@ __device__ __forceinline__ void visit_pair(const Sweep& c, Op& op, typename Op::
     }
 }
 
-// Steps whose loads a lane issues back to back before visiting them.
-#ifndef EMOGI_PIPELINE_STEPS
-#define EMOGI_PIPELINE_STEPS 4
-#endif
-constexpr int kSteps = EMOGI_PIPELINE_STEPS;
+// Steps whose loads (and neighbour reads) a lane issues back to back before
+// it updates any neighbour: Op::kSteps.  Measured on GB300 (uniform degree-32
+// graph): 4 helps top-down BFS from HBM (8.5 -> 7.6 ms) and changes nothing
+// from host memory; for SSSP and CC more steps only cost registers
+// (SSSP: 46 -> 91 registers, 5 -> 2 blocks per SM).
 
 // ------------------------------------------------------------------ kernels
 // Merged + aligned expansion with G lanes per vertex (G = 4, 8, 16, 32).
@@ -467,16 +478,16 @@ __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
         }
         const uint32_t steps = e > s ? (uint32_t)((e - a + 2 * G - 1) / (2 * G)) : 0u;
         const uint32_t maxsteps = __reduce_max_sync(0xffffffffu, steps);
-        for (uint32_t t0 = 0; t0 < maxsteps; t0 += kSteps) {
-            PairLoad p[kSteps];
-            uint2 cur[kSteps];
+        for (uint32_t t0 = 0; t0 < maxsteps; t0 += Op::kSteps) {
+            PairLoad p[Op::kSteps];
+            uint2 cur[Op::kSteps];
 #pragma unroll
-            for (int u = 0; u < kSteps; u++)
+            for (int u = 0; u < Op::kSteps; u++)
                 p[u] = load_pair<Op>(c, a + (uint64_t)(t0 + u) * (2 * G) + 2 * glane, s, e, t0 + u < steps);
 #pragma unroll
-            for (int u = 0; u < kSteps; u++) cur[u] = peek_pair(op, p[u]);
+            for (int u = 0; u < Op::kSteps; u++) cur[u] = peek_pair(op, p[u]);
 #pragma unroll
-            for (int u = 0; u < kSteps; u++) visit_pair(c, op, st, v, p[u], cur[u]);
+            for (int u = 0; u < Op::kSteps; u++) visit_pair(c, op, st, v, p[u], cur[u]);
         }
     }
     add_scanned(c, scanned);
@@ -514,15 +525,15 @@ __device__ __forceinline__ void expand_split_body(const Sweep& c, Op& op) {
         uint64_t ce = cs + 16ull * c.chunk_lines;
         if (ce > e) ce = e;
         const typename Op::S st = (typename Op::S)c.lq_state[lo];
-        for (uint64_t j0 = cs; j0 < ce; j0 += 64 * kSteps) {
-            PairLoad p[kSteps];
-            uint2 cur[kSteps];
+        for (uint64_t j0 = cs; j0 < ce; j0 += 64 * Op::kSteps) {
+            PairLoad p[Op::kSteps];
+            uint2 cur[Op::kSteps];
 #pragma unroll
-            for (int u = 0; u < kSteps; u++) p[u] = load_pair<Op>(c, j0 + 64 * u + 2 * lane, s, ce, true);
+            for (int u = 0; u < Op::kSteps; u++) p[u] = load_pair<Op>(c, j0 + 64 * u + 2 * lane, s, ce, true);
 #pragma unroll
-            for (int u = 0; u < kSteps; u++) cur[u] = peek_pair(op, p[u]);
+            for (int u = 0; u < Op::kSteps; u++) cur[u] = peek_pair(op, p[u]);
 #pragma unroll
-            for (int u = 0; u < kSteps; u++) visit_pair(c, op, st, v, p[u], cur[u]);
+            for (int u = 0; u < Op::kSteps; u++) visit_pair(c, op, st, v, p[u], cur[u]);
         }
     }
     op.flush();
@@ -554,14 +565,24 @@ __global__ void __launch_bounds__(256) k_bfs_bottom_up(Sweep c, uint32_t* level,
     unsigned long long scanned = 0, lf = 0;
     for (uint64_t base = warp * GPW; base < n; base += nwarps * GPW) {
         const uint64_t v = base + grp;
-        uint64_t s = 0, e = 0;
+        uint64_t s = 0, e = 0, s0 = 0;
         if (v < n && level[v] == INF) {
             s = c.off[v];
             e = c.off[v + 1];
         }
+        s0 = s;
+        bool found = false;
+        if (c.heads) {
+            // the first kHeads neighbours are mirrored in GPU memory: check
+            // them there, and read the list from host memory only after them
+            bool hit = false;
+            if (glane < (uint32_t)kHeads && s + glane < e) hit = level[c.heads[v * kHeads + glane]] == L;
+            const unsigned hits = __ballot_sync(0xffffffffu, hit);
+            found = (hits & gmask) != 0;
+            s = s + kHeads < e ? s + kHeads : e;
+        }
         const uint64_t a = aligned_start(s, c.shift);
         const uint32_t steps = e > s ? (uint32_t)((e - a + 2 * G - 1) / (2 * G)) : 0u;
-        bool found = false;
         for (uint32_t t = 0; __any_sync(0xffffffffu, t < steps && !found); t++) {
             bool hit = false;
             if (t < steps && !found) {
@@ -583,7 +604,7 @@ __global__ void __launch_bounds__(256) k_bfs_bottom_up(Sweep c, uint32_t* level,
         }
         if (found && glane == 0) {
             level[v] = L + 1;
-            lf += e - s;
+            lf += e - s0;
             push(c.out_q, c.out_count, (uint32_t)v);
         }
     }
@@ -647,45 +668,42 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
     op.flush();
 }
 
-// SSSP far-pile split (the near frontier is empty): every pending far vertex
-// whose distance is below the new threshold T moves to the near frontier of
-// sweep `round`, the others stay in the far pile; vertices already expanded
-// with their current distance are dropped.  Each vertex is in the pile once,
-// and nothing else runs meanwhile, so plain updates suffice.
-__device__ __forceinline__ void far_split_body(const uint32_t* fq_in, const uint32_t* fcount_in, uint32_t* fq_out,
-                                               uint32_t* fcount_out, uint32_t* nq_out, uint32_t* ncount_out,
-                                               const uint32_t* dist, uint32_t* qround, uint32_t* fflag,
-                                               const uint32_t* xd, uint32_t T, uint32_t round, uint32_t* far_min) {
+__device__ __forceinline__ void far_split_body(uint32_t n, uint32_t* fflag, const uint32_t* dist, const uint32_t* xd,
+                                               uint32_t* qround, uint32_t T, uint32_t round, uint32_t* nq_out,
+                                               uint32_t* ncount_out, uint32_t* kept, uint32_t* far_min) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
-    const uint64_t k = *fcount_in;
-    uint32_t lmin = INF;
-    for (uint64_t base = tid - (threadIdx.x & 31); base < k; base += nt) {
-        const uint64_t i = base + (threadIdx.x & 31);
-        if (i < k) {
-            const uint32_t v = fq_in[i];
+    uint32_t lmin = INF, lkept = 0;
+    for (uint64_t base = tid - (threadIdx.x & 31); base < n; base += nt) {
+        const uint64_t v = base + (threadIdx.x & 31);
+        if (v < n && fflag[v]) {
             const uint32_t d = dist[v];
             if (d >= xd[v]) {
-                fflag[v] = 0u;
+                fflag[v] = 0u;  // already expanded with this distance
             } else if (d < T) {
                 fflag[v] = 0u;
                 qround[v] = round;  // queued for the next sweep
-                push(nq_out, ncount_out, v);
+                push(nq_out, ncount_out, (uint32_t)v);
             } else {
                 lmin = d < lmin ? d : lmin;
-                push(fq_out, fcount_out, v);
+                lkept++;
             }
         }
     }
     warp_atomic_min(far_min, lmin);
+    const uint32_t wk = __reduce_add_sync(0xffffffffu, lkept);
+    if ((threadIdx.x & 31) == 0 && wk) atomicAdd(kept, wk);
 }
 
-static __global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount_in, uint32_t* fq_out,
-                                   uint32_t* fcount_out, uint32_t* nq_out, uint32_t* ncount_out, const uint32_t* dist,
-                                   uint32_t* qround, uint32_t* fflag, const uint32_t* xd, uint32_t T, uint32_t round,
-                                   uint32_t* far_min) {
-    far_split_body(fq_in, fcount_in, fq_out, fcount_out, nq_out, ncount_out, dist, qround, fflag, xd, T, round,
-                   far_min);
+// SSSP far split over all vertices (the near frontier is empty): every
+// vertex flagged "far" whose distance is below the new threshold T moves to
+// the near frontier of sweep `round`, the others stay flagged (counted in
+// *kept); vertices already expanded with their current distance are dropped.
+// Nothing else runs meanwhile, so plain updates suffice.
+static __global__ void k_far_split(uint32_t n, uint32_t* fflag, const uint32_t* dist, const uint32_t* xd,
+                                   uint32_t* qround, uint32_t T, uint32_t round, uint32_t* nq_out,
+                                   uint32_t* ncount_out, uint32_t* kept, uint32_t* far_min) {
+    far_split_body(n, fflag, dist, xd, qround, T, round, nq_out, ncount_out, kept, far_min);
 }
 
 // ------------------------------------------------------------------ device-driven SSSP loop
@@ -695,7 +713,7 @@ static __global__ void k_far_split(const uint32_t* fq_in, const uint32_t* fcount
 // returns at once.  No host round trip separates iterations.
 struct SsspLoop {
     uint32_t side;        // near frontier parity
-    uint32_t fside;       // far pile parity
+    uint32_t fside;       // unused (kept for layout)
     uint32_t mode;        // 0 = sweep next, 1 = far split next, 2 = done
     uint32_t T;           // current threshold
     uint32_t sweeps;      // sweeps run (sweep stamp of the next sweep)
@@ -712,7 +730,6 @@ struct SsspLoop {
 struct SsspFixed {
     Sweep base;           // off, cols, w, shift, split-list queue, scanned
     uint32_t* q[2];
-    uint32_t* fq[2];
     uint32_t* qround;
     uint32_t* fflag;
     uint32_t* xd;
@@ -727,8 +744,7 @@ __device__ __forceinline__ void sssp_loop_views(const SsspFixed& f, const SsspLo
     s->out_q = f.q[L.side ^ 1];
     s->out_count = &ctr->qcount[L.side ^ 1];
     s->large = &ctr->large[0];
-    *op = SsspOp{L.dist, f.qround, f.fflag, f.xd, f.fq[L.fside], &ctr->fcount[L.fside], &ctr->far_min,
-                 &ctr->overflow, L.T, L.sweeps, INF};
+    *op = SsspOp{L.dist, f.qround, f.fflag, f.xd, &ctr->far_min, &ctr->overflow, L.T, L.sweeps, INF};
 }
 
 template <class Ctr, int G>
@@ -755,8 +771,8 @@ template <class Ctr>
 __global__ void __launch_bounds__(256) k_sssp_loop_far(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
     const SsspLoop L = *Lp;
     if (L.mode != 1) return;
-    far_split_body(f.fq[L.fside], &ctr->fcount[L.fside], f.fq[L.fside ^ 1], &ctr->fcount[L.fside ^ 1],
-                   f.q[L.side], &ctr->qcount[L.side], L.dist, f.qround, f.fflag, f.xd, L.T, L.sweeps, &ctr->far_min);
+    far_split_body(f.base.all_n, f.fflag, L.dist, f.xd, f.qround, L.T, L.sweeps, f.q[L.side], &ctr->qcount[L.side],
+                   &ctr->fcount[0], &ctr->far_min);
 }
 
 // One thread: account for the iteration that just ran, pick the next one
@@ -766,18 +782,19 @@ __global__ void __launch_bounds__(256) k_sssp_loop_far(SsspFixed f, const SsspLo
 template <class Ctr>
 __global__ void k_sssp_loop_control(SsspLoop* Lp, Ctr* ctr, cudaGraphConditionalHandle handle) {
     SsspLoop L = *Lp;
-    uint64_t nk = 0, fk = 0;
+    uint64_t nk = 0;
+    // far vertices are pending if the last split kept some or a sweep since
+    // sent some (it then lowered far_min below INF)
+    const bool far_pending = ctr->fcount[0] > 0 || ctr->far_min != INF;
     if (L.mode == 0) {
         L.window_work += ctr->qcount[L.side];
         nk = ctr->qcount[L.side ^ 1];
-        fk = ctr->fcount[L.fside];
         L.side ^= 1;
         L.sweeps++;
     } else {
-        L.fside ^= 1;
         nk = ctr->qcount[L.side];
-        fk = ctr->fcount[L.fside];
     }
+    const uint64_t fk = far_pending ? 1 : 0;
     L.iters++;
     unsigned long long now;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(now));
@@ -801,7 +818,7 @@ __global__ void k_sssp_loop_control(SsspLoop* Lp, Ctr* ctr, cudaGraphConditional
         if (Tn <= L.T) Tn = (uint64_t)L.T + 1;
         L.T = Tn < (uint64_t)INF ? (uint32_t)Tn : INF;
         ctr->qcount[L.side] = 0;
-        ctr->fcount[L.fside ^ 1] = 0;
+        ctr->fcount[0] = 0;
         ctr->far_min = INF;
     } else {
         L.mode = 2;
@@ -909,14 +926,18 @@ static __global__ void k_ms_reached_edges(const unsigned long long* visit, const
 
 // Sampled CC, first phase: every vertex is linked with its first `rounds`
 // neighbours (one or two ids, usually one 32-byte sector of the edge list).
-static __global__ void k_cc_sample(const uint64_t* off, const uint64_t* cols, uint32_t* parent, uint32_t n,
-                                   uint32_t rounds, unsigned long long* scanned) {
+static __global__ void k_cc_sample(const uint64_t* off, const uint64_t* cols, const uint32_t* heads, uint32_t* parent,
+                                   uint32_t n, uint32_t rounds, unsigned long long* scanned) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     unsigned long long cnt = 0;
     for (uint64_t v = tid; v < n; v += nt) {
         const uint64_t s = off[v], e = off[v + 1];
         const uint64_t k = e - s < rounds ? e - s : rounds;
+        if (heads) {  // the ids are mirrored in GPU memory: no edge-list read
+            for (uint64_t r = 0; r < k; r++) uf_union(parent, (uint32_t)v, heads[v * kHeads + r]);
+            continue;
+        }
         for (uint64_t r = 0; r < k; r++) uf_union(parent, (uint32_t)v, (uint32_t)ld_edge(cols + s + r));
         cnt += k;
     }

@@ -21,7 +21,7 @@ constexpr int kThreads = 256;
 // SSSP windows that expanded fewer than n >> EMOGI_SSSP_LIGHT_SHIFT vertices
 // make the next window wider (0 = fixed windows).
 #ifndef EMOGI_SSSP_LIGHT_SHIFT
-#define EMOGI_SSSP_LIGHT_SHIFT 16
+#define EMOGI_SSSP_LIGHT_SHIFT 0
 #endif
 constexpr uint32_t kLargeLines = 32;  // lists above 32 lines (4 KiB) are split
 
@@ -110,6 +110,7 @@ Sweep make_sweep(const Ctx& c, int side, bool all_vertices) {
     s.large_lines = kLargeLines;
     s.chunk_lines = c.chunk;
     s.scanned = &ws.ctr->scanned;
+    s.heads = g->d_heads;
     return s;
 }
 
@@ -273,8 +274,6 @@ emogi_status build_sssp_exec(Ctx& c) {
     f.base = make_sweep(c, 0, false);
     f.q[0] = ws.q[0];
     f.q[1] = ws.q[1];
-    f.fq[0] = ws.fq[0];
-    f.fq[1] = ws.fq[1];
     f.qround = ws.flag;
     f.fflag = ws.fflag;
     f.xd = ws.xd;
@@ -441,7 +440,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         c.kernel_launches += 4ull * it;
     }
     uint64_t T = std::min<uint64_t>(delta, dev::INF);
-    int side = 0, fside = 0;
+    int side = 0;
     uint64_t nk = device_loop ? 0 : 1, fk = 0;
     // Window widths adapt to the work they carry: a window whose sweeps
     // expanded very few vertices (under n/65536: the first hops from the
@@ -460,14 +459,13 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         if (nk > 0) {
             EMOGI_TRY(reset_sweep_counters(c, side));
             Sweep s = make_sweep(c, side, false);
-            dev::SsspOp op{state,          qround,            ws.fflag,       ws.xd,       ws.fq[fside],
-                           &ctr->fcount[fside], &ctr->far_min, &ctr->overflow, (uint32_t)T, sweeps, dev::INF};
+            dev::SsspOp op{state, qround, ws.fflag, ws.xd, &ctr->far_min, &ctr->overflow, (uint32_t)T, sweeps, dev::INF};
             EMOGI_TRY(sweep(c, s, op, nk));
             sweeps++;
             window_work += nk;
             EMOGI_TRY(read_counters(c));
             nk = ws.h_ctr->qcount[side ^ 1];
-            fk = ws.h_ctr->fcount[fside];
+            fk = (ws.h_ctr->fcount[0] > 0 || ws.h_ctr->far_min != dev::INF) ? 1 : 0;
             side ^= 1;
         } else {
             // near frontier empty: raise T past the smallest pending far distance
@@ -479,17 +477,17 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
             if (Tn <= T) Tn = T + 1;
             T = std::min<uint64_t>(Tn, dev::INF);
             EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->qcount[side], 0, sizeof(uint32_t), c.st));
-            EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->fcount[fside ^ 1], 0, sizeof(uint32_t), c.st));
+            EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->fcount[0], 0, sizeof(uint32_t), c.st));
             EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->far_min, 0xFF, sizeof(uint32_t), c.st));
-            dev::k_far_split<<<grid_for(c, fk), kThreads, 0, c.st>>>(
-                ws.fq[fside], &ctr->fcount[fside], ws.fq[fside ^ 1], &ctr->fcount[fside ^ 1], ws.q[side],
-                &ctr->qcount[side], state, qround, ws.fflag, ws.xd, (uint32_t)T, sweeps, &ctr->far_min);
+            dev::k_far_split<<<grid_for(c, n), kThreads, 0, c.st>>>((uint32_t)n, ws.fflag, state, ws.xd, qround,
+                                                                     (uint32_t)T, sweeps, ws.q[side],
+                                                                     &ctr->qcount[side], &ctr->fcount[0],
+                                                                     &ctr->far_min);
             EMOGI_CUDA_TRY(cudaGetLastError());
             c.kernel_launches++;
             EMOGI_TRY(read_counters(c, false));
-            fside ^= 1;
             nk = ws.h_ctr->qcount[side];
-            fk = ws.h_ctr->fcount[fside];
+            fk = ws.h_ctr->fcount[0] > 0 ? 1 : 0;
         }
         it++;
     }
@@ -620,7 +618,7 @@ emogi_status emogi_cc(emogi_graph g, uint32_t* label, const emogi_opts* opts, em
         if (sampled) {
             const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
             if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
-            dev::k_cc_sample<<<grid_for(c, n), kThreads, 0, c.st>>>(g->d_off, g->cols, parent, n, 2,
+            dev::k_cc_sample<<<grid_for(c, n), kThreads, 0, c.st>>>(g->d_off, g->cols, g->d_heads, parent, n, 2,
                                                                      &ws.ctr->scanned);
             EMOGI_CUDA_TRY(cudaGetLastError());
             if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[3], c.st));

@@ -26,7 +26,7 @@ OK, E_ARG, E_NOMEM, E_BUDGET, E_CUDA, E_TIMEOUT, E_OVERFLOW, E_UNSUPPORTED = ran
 PLACE_DEVICE, PLACE_HOST, PLACE_MANAGED = 0, 1, 2
 PLACEMENTS = {"device": PLACE_DEVICE, "host": PLACE_HOST, "managed": PLACE_MANAGED}
 # load flags
-LOAD_UNDIRECTED, LOAD_BORROW = 1, 2
+LOAD_UNDIRECTED, LOAD_BORROW, LOAD_NO_HEADS = 1, 2, 4
 # emogi_access
 ACCESS_MERGED_ALIGNED, ACCESS_MERGED, ACCESS_NAIVE = 0, 1, 2
 ACCESS = {"merged_aligned": ACCESS_MERGED_ALIGNED, "aligned": ACCESS_MERGED_ALIGNED,
@@ -212,10 +212,12 @@ class Graph:
 
 
 def load_csr(n, m, row_offsets, col_idx, weights=None, placement="host", flags=0,
-             undirected: Optional[bool] = None, borrow: bool = False) -> Graph:
+             undirected: Optional[bool] = None, borrow: bool = False, heads: bool = True) -> Graph:
     """emogi_load_csr: copy (or, with borrow, pin in place) a CSR graph."""
     place = PLACEMENTS[placement] if isinstance(placement, str) else int(placement)
     f = int(flags)
+    if not heads:
+        f |= LOAD_NO_HEADS
     if undirected:
         f |= LOAD_UNDIRECTED
     if borrow:
@@ -233,11 +235,11 @@ def load_csr(n, m, row_offsets, col_idx, weights=None, placement="host", flags=0
     return Graph(h.value, int(n), int(m), place, keep)
 
 
-def load_graph(g, placement="host", borrow=False, with_weights=True) -> Graph:
+def load_graph(g, placement="host", borrow=False, with_weights=True, heads=True) -> Graph:
     """Load a graphgen.Graph-like object (n, offsets, cols, weights, undirected)."""
     w = g.weights if with_weights else None
     return load_csr(g.n, g.m, g.offsets, g.cols, w, placement=placement,
-                    undirected=bool(getattr(g, "undirected", False)), borrow=borrow)
+                    undirected=bool(getattr(g, "undirected", False)), borrow=borrow, heads=heads)
 
 
 def _opts(access=None, granularity=0, chunk_lines=0, timeout_ns=0, stream=None, out_on_device=False,

@@ -525,3 +525,27 @@ def test_cc_sampled_and_full_pass(placement, name):
             _, full = E.cc(h, cc_full_pass=True)
             _, smp = E.cc(h)
             assert smp["edges_scanned"] < 0.5 * full["edges_scanned"]
+
+
+@pytest.mark.parametrize("placement", ["host", "managed"])
+@pytest.mark.parametrize("name", ["kron16", "urand14", "hub", "path", "residues-sym", "many"])
+def test_list_heads_on_and_off(placement, name):
+    """The first four ids of every list mirrored in GPU memory (used by sampled
+    CC and bottom-up BFS) change how much is read over the host link, never
+    the result."""
+    if name == "many":
+        g = many_components_graph()
+    elif name == "residues-sym":
+        r = graph("residues")
+        deg = np.diff(r.offsets).astype(np.int64)
+        g = gg.csr_from_edges(r.n, np.repeat(np.arange(r.n), deg), r.cols, symmetrize=True, dedup=False,
+                              drop_self_loops=False)
+    else:
+        g = graph(name)
+    exp_cc = oracle.cc_g(g)
+    for heads in (True, False):
+        with E.load_graph(g, placement=placement, heads=heads, with_weights=False) as h:
+            for s in sources(g):
+                np.testing.assert_array_equal(E.bfs(h, s)[0], oracle.bfs_g(g, s), err_msg=f"heads={heads} src={s}")
+                np.testing.assert_array_equal(E.bfs(h, s, granularity=4)[0], oracle.bfs_g(g, s))
+            np.testing.assert_array_equal(E.cc(h)[0], exp_cc, err_msg=f"heads={heads}")
