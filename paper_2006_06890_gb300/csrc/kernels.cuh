@@ -427,15 +427,29 @@ __device__ __forceinline__ uint2 peek_pair(const Op& op, const PairLoad& p) {
     return cur;
 }
 
+// Full-warp append of up to two ids per lane, called where the whole warp is
+// converged: one atomicAdd per warp per call however the lanes diverged in
+// their updates, and each lane's slots from a ballot prefix count.
+__device__ __forceinline__ void warp_push2(uint32_t* q, uint32_t* count, bool p0, uint32_t id0, bool p1,
+                                           uint32_t id1) {
+    const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
+    const uint32_t total = __popc(b0) + __popc(b1);
+    if (total == 0) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(count, total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const unsigned below = (1u << lane) - 1u;
+    if (p0) q[base + __popc(b0 & below)] = id0;
+    if (p1) q[base + __popc(b0) + __popc(b1 & below)] = id1;
+}
+
 template <class Op>
 __device__ __forceinline__ void visit_pair(const Sweep& c, Op& op, typename Op::S st, uint32_t v, const PairLoad& p,
                                            uint2 cur) {
     const bool p0 = (p.valid & 1u) && op.visit(st, v, p.id.x, p.w.x, cur.x);
     const bool p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y, cur.y);
-    if (Op::kPush) {
-        if (p0) push(c.out_q, c.out_count, (uint32_t)p.id.x);
-        if (p1) push(c.out_q, c.out_count, (uint32_t)p.id.y);
-    }
+    if (Op::kPush) warp_push2(c.out_q, c.out_count, p0, (uint32_t)p.id.x, p1, (uint32_t)p.id.y);
 }
 
 // Steps whose loads (and neighbour reads) a lane issues back to back before
