@@ -221,6 +221,9 @@ def time_loop(torch, E, h, srcs, stream, steps, warmup, outs):
     return e0.elapsed_time(e1), wall, per
 
 
+VARIANT_STEPS = 4  # sources each comparison variant is timed on (after one untimed step)
+
+
 def ours(args):
     import torch
 
@@ -310,11 +313,17 @@ def ours(args):
                          ("merged_zero_copy", dict(placement="host", access="merged")),
                          ("aligned_zero_copy_paper_forms", dict(placement="host", access="merged_aligned",
                                                                 top_down_only=True, cc_full_pass=True)),
+                         ("aligned_zero_copy_beamer_rule", dict(placement="host", access="merged_aligned",
+                                                                beamer=True)),
+                         ("aligned_zero_copy_ids32", dict(placement="host", access="merged_aligned", ids32=True)),
                          ("managed_uvm", dict(placement="managed", access="merged_aligned")),
-                         ("device_hbm", dict(placement="device", access="merged_aligned"))):
+                         ("device_hbm", dict(placement="device", access="merged_aligned")),
+                         ("device_hbm_ids32", dict(placement="device", access="merged_aligned", ids32=True))):
             try:
-                hv = h if kw["placement"] == "host" else E.load_graph(g, placement=kw["placement"])
-                okw = {k: v for k, v in kw.items() if k != "placement"}
+                ids32 = kw.get("ids32", False)
+                hv = h if (kw["placement"] == "host" and not ids32) else \
+                    E.load_graph(g, placement=kw["placement"], ids32=ids32)
+                okw = {k: v for k, v in kw.items() if k not in ("placement", "ids32")}
 
                 def one(src):
                     sb = E.bfs(hv, src, stream=stream, out=outs[0], **okw)[1]
@@ -325,12 +334,16 @@ def ours(args):
                 t0 = time.perf_counter()
                 first = one(srcs[0])  # cold for managed: pages migrate
                 cold_s = time.perf_counter() - t0
-                st = one(srcs[1])
-                tot_ms = sum(s["ms"] for s in st)
-                variants[name] = {"gteps": round(step_teps_edges(st) / (tot_ms * 1e-3) / 1e9, 4),
-                                  "ms_per_step": round(tot_ms, 3), "first_step_s": round(cold_s, 3),
-                                  "bfs_ms": round(st[0]["ms"], 3), "sssp_ms": round(st[1]["ms"], 3),
-                                  "cc_ms": round(st[2]["ms"], 3)}
+                sts = [one(x) for x in srcs[1:1 + VARIANT_STEPS]]
+                tot_ms = sum(s["ms"] for st in sts for s in st)
+                edges = sum(step_teps_edges(st) for st in sts)
+                k = len(sts)
+                variants[name] = {"gteps": round(edges / (tot_ms * 1e-3) / 1e9, 4),
+                                  "ms_per_step": round(tot_ms / k, 3), "first_step_s": round(cold_s, 3),
+                                  "steps": k,
+                                  "bfs_ms": round(sum(st[0]["ms"] for st in sts) / k, 3),
+                                  "sssp_ms": round(sum(st[1]["ms"] for st in sts) / k, 3),
+                                  "cc_ms": round(sum(st[2]["ms"] for st in sts) / k, 3)}
                 del first
                 if hv is not h:
                     hv.free()
@@ -629,9 +642,10 @@ def ncu_case(args):
     with E.load_graph(g, placement="host") as h:
         sb = E.bfs(h, srcs[0], out=out)[1]
         ss = E.sssp(h, srcs[0], out=out)[1]
+        sh = E.sssp(h, srcs[0], out=out, host_loop=True)[1]  # sweeps as separate launches, for per-kernel counters
         sc = E.cc(h, out=out)[1]
     print(json.dumps({"ncu_case": f"uniform n=2^22 degree {args.degree}, host placement",
-                      "bfs": sb, "sssp": ss, "cc": sc}))
+                      "bfs": sb, "sssp": ss, "sssp_host_loop": sh, "cc": sc}))
 
 
 def kron27(args):

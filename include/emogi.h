@@ -88,10 +88,13 @@ enum {
     EMOGI_OPT_CC_FULL_PASS = 1u << 2,  /* CC: stream the whole edge list as the paper does instead of
                                           linking sampled neighbours first and skipping the vertices
                                           already in the largest sampled component */
-    EMOGI_OPT_HOST_LOOP = 1u << 3      /* SSSP: drive the sweep loop from the host (one counter
+    EMOGI_OPT_HOST_LOOP = 1u << 3,     /* SSSP: drive the sweep loop from the host (one counter
                                           readback per sweep, as the paper's level loop) instead of a
                                           recorded CUDA graph whose conditional loop decides on the
                                           device */
+    EMOGI_OPT_BEAMER = 1u << 4         /* BFS: choose each level's direction by the fixed thresholds
+                                          of Beamer et al. (alpha = 14, beta = 24) instead of the
+                                          estimate of list entries each direction would read */
 };
 
 /* Per-call options.  Pass NULL for defaults.  struct_size must be
@@ -118,7 +121,7 @@ typedef struct {
     uint32_t reserved;
     uint64_t edges_scanned; /* neighbour-list entries read by the expansion kernels */
     uint64_t edges_reached; /* sum of out-degrees of reached vertices (the TEPS numerator; m for CC) */
-    uint64_t edge_bytes;    /* edges_scanned * 8 */
+    uint64_t edge_bytes;    /* edges_scanned * bytes per id (8, or 4 for emogi_load_csr32) */
     uint64_t weight_bytes;  /* weights read (SSSP): edges_scanned * 4 */
     double ms;              /* device time of the traversal, CUDA events on the launch stream */
     double expand_ms;       /* with EMOGI_OPT_TIME_KERNELS: summed duration of expansion launches */
@@ -147,16 +150,35 @@ emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets,
                             const uint64_t* col_idx, const uint32_t* weights,
                             emogi_placement place, uint32_t flags, emogi_graph* out);
 
+/* Load a CSR graph whose edge list holds 4-byte ids (Sec. 5.4 compares the
+ * 4-byte edge list with the 8-byte one: it halves the link bytes of every id
+ * read; Sec. 4.1: a 128-byte line then holds 32 ids instead of 16).  The
+ * arguments, placement, flags, ownership and errors are those of
+ * emogi_load_csr, except:
+ *   col_idx      host uint32_t[m], every entry < n (with EMOGI_LOAD_BORROW,
+ *                16-byte aligned, kept alive and unchanged until
+ *                emogi_free_graph)
+ * Every traversal, emogi_msbfs, the batch and the server accept the handle
+ * and return exactly the results of the same graph loaded with 8-byte ids;
+ * the kernels read four ids per 16-byte lane load and align list reads to
+ * 32-id lines.  emogi_bfs_noalloc takes uint64 ids only. */
+emogi_status emogi_load_csr32(uint64_t n, uint64_t m, const uint64_t* row_offsets,
+                              const uint32_t* col_idx, const uint32_t* weights,
+                              emogi_placement place, uint32_t flags, emogi_graph* out);
+
 /* Breadth-first search from src (Sec. 2.1, Algorithm "High-level Graph
  * Traversal Flow" with the BFS condition: an unvisited neighbour of an active
  * vertex becomes active at the next depth; one kernel round per level, Sec. 4.2).
  * On graphs loaded with EMOGI_LOAD_UNDIRECTED and MERGED_ALIGNED access, a
- * level whose frontier holds more edges than 1/14 of the unreached vertices'
- * edges is expanded bottom-up instead (every unreached vertex reads its own
- * list up to its first neighbour on the current level) until the frontier
- * falls below n/24 vertices (direction-optimising BFS, Beamer et al. 2012);
- * EMOGI_OPT_TOP_DOWN_ONLY keeps the paper's push-only form.  The levels are
- * the same either way.
+ * level is expanded bottom-up instead (every unreached vertex reads its own
+ * list up to its first neighbour on the current level; direction-optimising
+ * BFS, Beamer et al. 2012) when that is estimated to read fewer list entries
+ * than the frontier's own lists hold: with p the frontier's share of edge
+ * endpoints, an unreached vertex of mean degree d reads about
+ * sum_{i<d} (1-p)^i entries, the first four of them from GPU memory when the
+ * list heads are mirrored there.  EMOGI_OPT_BEAMER uses Beamer's fixed
+ * thresholds instead; EMOGI_OPT_TOP_DOWN_ONLY keeps the paper's push-only
+ * form.  The levels are the same either way.
  *   level  uint32_t[n] output (host, or device if opts->out_on_device):
  *          level[src] = 0, hop distance for reached vertices, EMOGI_INF otherwise.
  * Errors: EMOGI_E_ARG (src >= n, NULL pointer), EMOGI_E_BUDGET, EMOGI_E_NOMEM,

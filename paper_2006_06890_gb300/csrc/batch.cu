@@ -25,10 +25,12 @@ namespace {
 
 struct BatchGraph {
     const uint64_t* off;
-    const uint64_t* cols;
+    const void* cols;
     uint64_t base;   // first entry of this graph in the combined level array
     uint32_t n;
     uint32_t shift;
+    uint32_t ids32;  // 1: uint32 ids, 0: uint64 ids
+    uint32_t pad;
 };
 
 struct BatchCtl {
@@ -145,7 +147,7 @@ __global__ void __launch_bounds__(256) k_batch_bfs(BatchParams p) {
             for (uint32_t c0 = base; c0 < base + step && c0 < k; c0 += GPW) {
                 const uint32_t idx = c0 + grp;
                 uint64_t s = 0, e = 0, a = 0;
-                BatchGraph d = {nullptr, nullptr, 0, 0, 0};
+                BatchGraph d = {nullptr, nullptr, 0, 0, 0, 0, 0};
                 uint32_t v = 0, gi = 0;
                 if (idx < k && idx < base + step) {
                     const uint2 en = in_q[idx];
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(256) k_batch_bfs(BatchParams p) {
                     d = p.graphs[gi];
                     s = d.off[v];
                     e = d.off[v + 1];
-                    a = dev::aligned_start(s, d.shift);
+                    a = d.ids32 ? dev::aligned_start<uint32_t>(s, d.shift) : dev::aligned_start<uint64_t>(s, d.shift);
                     if (glane == 0) scanned += e - s;
                 }
                 const uint32_t steps = e > s ? (uint32_t)((e - a + 2 * G - 1) / (2 * G)) : 0u;
@@ -162,17 +164,24 @@ __global__ void __launch_bounds__(256) k_batch_bfs(BatchParams p) {
                 uint32_t* lev = p.level + d.base;
                 for (uint32_t t = 0; t < maxsteps; t++) {
                     const uint64_t j = a + (uint64_t)t * (2 * G) + 2 * glane;
-                    uint64_t u[2] = {0, 0};
+                    // two ids per lane and step: 16 bytes of uint64 ids or 8 of uint32
+                    uint32_t u[2] = {0, 0};
                     bool ok[2] = {false, false};
                     if (t < steps && j + 1 >= s) {
                         if (j + 1 < e) {
-                            const ulonglong2 pr = dev::ld_edge2(d.cols + j);
-                            u[0] = pr.x;
-                            u[1] = pr.y;
+                            if (d.ids32) {
+                                const uint2 pr = dev::ld_w2((const uint32_t*)d.cols + j);
+                                u[0] = pr.x;
+                                u[1] = pr.y;
+                            } else {
+                                const ulonglong2 pr = dev::ld_edge2((const uint64_t*)d.cols + j);
+                                u[0] = (uint32_t)pr.x;
+                                u[1] = (uint32_t)pr.y;
+                            }
                             ok[0] = j >= s;
                             ok[1] = true;
                         } else if (j < e && j >= s) {
-                            u[0] = dev::ld_edge(d.cols + j);
+                            u[0] = d.ids32 ? dev::ld_id<uint32_t>(d.cols, j) : dev::ld_id<uint64_t>(d.cols, j);
                             ok[0] = true;
                         }
                     }
@@ -387,7 +396,8 @@ emogi_status emogi_batch_create(const emogi_graph* graphs, uint32_t count, emogi
             return fail(EMOGI_E_ARG, "all graphs of a batch must be on one device");
         }
         b->base[g] = b->total;
-        table[g] = BatchGraph{gr->d_off, gr->cols, b->total, (uint32_t)gr->n, gr->shift};
+        table[g] = BatchGraph{gr->d_off, gr->cols, b->total, (uint32_t)gr->n, gr->shift,
+                              gr->id_bytes == 4 ? 1u : 0u, 0u};
         b->total += gr->n;
     }
     if (b->total >= 0xFFFFFFFFull) {

@@ -116,8 +116,9 @@ emogi_status ensure_workspace(emogi_graph g) {
     const uint64_t n = g->n ? g->n : 1;
     ws.n = n;
     // split-list vertices: a list is split when its aligned span exceeds 32
-    // lines (512 ids); the span starts at most 15 ids before the list, so a
-    // split list holds at least 498 ids and one sweep splits at most m / 498
+    // lines (512 uint64 ids or 1024 uint32 ids); the span starts at most 15
+    // (31) ids before the list, so a split list holds at least 498 ids and
+    // one sweep splits at most m / 498
     ws.lq_cap = std::min<uint64_t>(n, g->m / 497 + 1);
     struct Item { void** p; size_t bytes; const char* what; };
     Item items[] = {
@@ -181,7 +182,8 @@ void release_workspace(emogi_graph g) {
 // ---------------------------------------------------------------- validation
 // Checks the CSR in parallel on the host: offsets monotone from 0 to m, every
 // column id below n.
-static emogi_status validate_csr(uint64_t n, uint64_t m, const uint64_t* off, const uint64_t* cols) {
+template <class Id>
+static emogi_status validate_csr(uint64_t n, uint64_t m, const uint64_t* off, const Id* cols) {
     if (off[0] != 0) return fail(EMOGI_E_ARG, "row_offsets[0] = %llu, expected 0", (unsigned long long)off[0]);
     if (off[n] != m)
         return fail(EMOGI_E_ARG, "row_offsets[n] = %llu but m = %llu", (unsigned long long)off[n],
@@ -307,7 +309,8 @@ static emogi_status place_array(int place, bool borrow, int device, const void* 
 // heads[v * 4 + r] = col_idx[row_offsets[v] + r] for r < degree, else
 // UINT32_MAX; gathered on the host from the caller's arrays (no device read
 // of the placed edge list, so a managed edge list is not migrated by this).
-static emogi_status build_heads(emogi_graph g, const uint64_t* off, const uint64_t* cols) {
+template <class Id>
+static emogi_status build_heads(emogi_graph g, const uint64_t* off, const Id* cols) {
     const uint64_t n = g->n;
     std::vector<uint32_t> h;
     try {
@@ -342,39 +345,11 @@ static void release_array(int place, void* owned, const void* borrowed, size_t b
 
 }  // namespace emogi
 
-using namespace emogi;
+namespace emogi {
 
-extern "C" {
-
-const char* emogi_status_string(emogi_status s) {
-    switch (s) {
-        case EMOGI_OK: return "EMOGI_OK";
-        case EMOGI_E_ARG: return "EMOGI_E_ARG";
-        case EMOGI_E_NOMEM: return "EMOGI_E_NOMEM";
-        case EMOGI_E_BUDGET: return "EMOGI_E_BUDGET";
-        case EMOGI_E_CUDA: return "EMOGI_E_CUDA";
-        case EMOGI_E_TIMEOUT: return "EMOGI_E_TIMEOUT";
-        case EMOGI_E_OVERFLOW: return "EMOGI_E_OVERFLOW";
-        case EMOGI_E_UNSUPPORTED: return "EMOGI_E_UNSUPPORTED";
-    }
-    return "EMOGI_E_UNKNOWN";
-}
-
-const char* emogi_last_error(void) { return t_last_error.c_str(); }
-
-const char* emogi_version(void) { return "emogi-gb300 0.1 (sm_103a)"; }
-
-emogi_status emogi_set_device_budget(uint64_t bytes) {
-    g_budget = bytes;
-    return EMOGI_OK;
-}
-
-uint64_t emogi_device_bytes_in_use(void) { return g_in_use.load(); }
-
-void emogi_test_fail_device_alloc_after(int k) { g_fail_after = k > 0 ? k : 0; }
-
-emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets, const uint64_t* col_idx,
-                            const uint32_t* weights, emogi_placement place, uint32_t flags, emogi_graph* out) {
+template <class Id>
+static emogi_status load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets, const Id* col_idx,
+                             const uint32_t* weights, emogi_placement place, uint32_t flags, emogi_graph* out) {
     clear_error();
     if (!out) return fail(EMOGI_E_ARG, "out is NULL");
     *out = nullptr;
@@ -414,11 +389,12 @@ emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets,
 
     // edge list (and weights) by placement (Sec. 3.1, Sec. 5.1.2)
     const void* kp = nullptr;
-    s = place_array(place, borrow, g->device, col_idx, m * sizeof(uint64_t), &kp, &g->cols_owned,
+    g->id_bytes = sizeof(Id);
+    s = place_array(place, borrow, g->device, col_idx, m * sizeof(Id), &kp, &g->cols_owned,
                     &g->cols_borrowed, &g->dev_bytes, "edge list");
     if (s != EMOGI_OK) return bail(s);
-    g->cols = (const uint64_t*)kp;
-    g->shift = (uint32_t)(((uintptr_t)g->cols % 128) / 8);
+    g->cols = kp;
+    g->shift = (uint32_t)(((uintptr_t)g->cols % 128) / sizeof(Id));
     if (weights) {
         // mean weight from up to 2^20 evenly spaced entries
         const uint64_t stride = m > (1u << 20) ? m / (1u << 20) : 1;
@@ -445,6 +421,49 @@ emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets,
     return EMOGI_OK;
 }
 
+}  // namespace emogi
+
+using namespace emogi;
+
+extern "C" {
+
+const char* emogi_status_string(emogi_status s) {
+    switch (s) {
+        case EMOGI_OK: return "EMOGI_OK";
+        case EMOGI_E_ARG: return "EMOGI_E_ARG";
+        case EMOGI_E_NOMEM: return "EMOGI_E_NOMEM";
+        case EMOGI_E_BUDGET: return "EMOGI_E_BUDGET";
+        case EMOGI_E_CUDA: return "EMOGI_E_CUDA";
+        case EMOGI_E_TIMEOUT: return "EMOGI_E_TIMEOUT";
+        case EMOGI_E_OVERFLOW: return "EMOGI_E_OVERFLOW";
+        case EMOGI_E_UNSUPPORTED: return "EMOGI_E_UNSUPPORTED";
+    }
+    return "EMOGI_E_UNKNOWN";
+}
+
+const char* emogi_last_error(void) { return t_last_error.c_str(); }
+
+const char* emogi_version(void) { return "emogi-gb300 0.1 (sm_103a)"; }
+
+emogi_status emogi_set_device_budget(uint64_t bytes) {
+    g_budget = bytes;
+    return EMOGI_OK;
+}
+
+uint64_t emogi_device_bytes_in_use(void) { return g_in_use.load(); }
+
+void emogi_test_fail_device_alloc_after(int k) { g_fail_after = k > 0 ? k : 0; }
+
+emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets, const uint64_t* col_idx,
+                            const uint32_t* weights, emogi_placement place, uint32_t flags, emogi_graph* out) {
+    return load_csr<uint64_t>(n, m, row_offsets, col_idx, weights, place, flags, out);
+}
+
+emogi_status emogi_load_csr32(uint64_t n, uint64_t m, const uint64_t* row_offsets, const uint32_t* col_idx,
+                              const uint32_t* weights, emogi_placement place, uint32_t flags, emogi_graph* out) {
+    return load_csr<uint32_t>(n, m, row_offsets, col_idx, weights, place, flags, out);
+}
+
 emogi_status emogi_free_graph(emogi_graph g) {
     if (!g) return EMOGI_OK;
     cudaSetDevice(g->device);
@@ -452,7 +471,7 @@ emogi_status emogi_free_graph(emogi_graph g) {
     release_workspace(g);
     if (!g->shared) {
         if (g->d_heads) dev_free(g->d_heads, g->n * 4 * sizeof(uint32_t));
-        release_array(g->place, g->cols_owned, g->cols_borrowed, g->m * sizeof(uint64_t));
+        release_array(g->place, g->cols_owned, g->cols_borrowed, g->m * g->id_bytes);
         if (g->w || g->w_owned || g->w_borrowed)
             release_array(g->place, g->w_owned, g->w_borrowed, g->m * sizeof(uint32_t));
         if (g->d_off) dev_free(g->d_off, (g->n + 1) * sizeof(uint64_t));
@@ -478,6 +497,7 @@ emogi_status emogi_graph_share(emogi_graph g, emogi_graph* out) {
     h->d_off = g->d_off;
     h->d_heads = g->d_heads;
     h->cols = g->cols;
+    h->id_bytes = g->id_bytes;
     h->w = g->w;
     h->shift = g->shift;
     h->avg_degree = g->avg_degree;

@@ -108,13 +108,14 @@ struct emogi_graph_s {
     int place = EMOGI_PLACE_DEVICE;
     uint64_t* d_off = nullptr;         // device row offsets (n + 1)
     uint32_t* d_heads = nullptr;       // first 4 ids of every list in GPU memory (edge lists off the GPU)
-    const uint64_t* cols = nullptr;    // kernel-visible edge list
+    const void* cols = nullptr;        // kernel-visible edge list (uint64 or uint32 ids)
+    uint32_t id_bytes = 8;             // bytes per id: 8, or 4 for a graph loaded by emogi_load_csr32
     const uint32_t* w = nullptr;       // kernel-visible weights or null
     void* cols_owned = nullptr;        // what to free (device / pinned / managed)
     void* w_owned = nullptr;
     const void* cols_borrowed = nullptr;  // what to unregister
     const void* w_borrowed = nullptr;
-    uint32_t shift = 0;                // (edge-list base address mod 128) / 8
+    uint32_t shift = 0;                // (edge-list base address mod 128) / id_bytes
     size_t dev_bytes = 0;              // budgeted device bytes of the graph arrays
     cudaStream_t stream = nullptr;
     emogi::Workspace ws;

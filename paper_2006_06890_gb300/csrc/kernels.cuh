@@ -38,9 +38,9 @@ constexpr unsigned long long CHUNK_MASK = (1ull << SLOT_SHIFT) - 1;
 // Everything a sweep needs besides the per-application state.
 struct Sweep {
     const uint64_t* off = nullptr;       // row offsets (GPU memory)
-    const uint64_t* cols = nullptr;      // edge list (GPU, pinned host or managed memory)
+    const void* cols = nullptr;          // edge list of uint64 or uint32 ids (GPU, pinned host or managed)
     const uint32_t* w = nullptr;         // weights beside the edges, or null
-    uint32_t shift = 0;                  // (edge-list base address mod 128) / 8
+    uint32_t shift = 0;                  // (edge-list base address mod 128) / bytes per id
     const uint32_t* in_q = nullptr;      // active vertices, or null for "all vertices"
     const uint32_t* in_count = nullptr;  // number of active vertices (when in_q != null)
     uint32_t all_n = 0;                  // number of vertices (when in_q == null)
@@ -61,41 +61,93 @@ constexpr int kHeads = 4;
 
 // ------------------------------------------------------------------ loads
 // Edge-list reads go through the non-coherent read-only path and do not
-// allocate in L1: every line is used once per sweep.  The edge list and the
-// weights never change during a traversal, so these loads are free of side
-// effects and the compiler may schedule them early.
+// allocate in L1: every line is used once per sweep.  They are volatile so
+// that they issue where they are written, all of a lane's loads of a batch
+// before its first neighbour read: left free, the compiler sinks a weight
+// load to its use after the neighbour reads (fewer live registers), which
+// adds a second host-link round trip to every step (measured on GB300: the
+// largest SSSP sweep from host memory 11.8 -> 18.2 ms).
+//
+// Ids are uint64 (the paper's main format) or uint32 (the 4-byte edge list
+// of Sec. 5.4, 32 ids per 128-byte line as Sec. 4.1 counts them, which halves
+// the link bytes of an id); either way a
+// lane reads 16 bytes per step: two 8-byte or four 4-byte ids, plus the same
+// number of 4-byte weights.  Vertex ids are below 2^32 in both formats, so
+// the loaded ids are narrowed to uint32 at once.
+template <class Id> struct IdWidth;
+template <> struct IdWidth<uint64_t> {
+    static constexpr int kPerStep = 2;   // ids per 16-byte lane load
+    static constexpr int kPerLine = 16;  // ids per 128-byte line
+};
+template <> struct IdWidth<uint32_t> {
+    static constexpr int kPerStep = 4;
+    static constexpr int kPerLine = 32;
+};
+
 __device__ __forceinline__ ulonglong2 ld_edge2(const uint64_t* p) {
     ulonglong2 r;
-    asm("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];"
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];"
                  : "=l"(r.x), "=l"(r.y)
                  : "l"(p));
     return r;
 }
 __device__ __forceinline__ uint64_t ld_edge(const uint64_t* p) {
     uint64_t r;
-    asm("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(r) : "l"(p));
+    asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(r) : "l"(p));
     return r;
 }
 __device__ __forceinline__ uint2 ld_w2(const uint32_t* p) {
     uint2 r;
-    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];"
+    asm volatile("ld.global.nc.L1::no_allocate.v2.u32 {%0, %1}, [%2];"
                  : "=r"(r.x), "=r"(r.y)
+                 : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint4 ld_u32x4(const uint32_t* p) {
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
                  : "l"(p));
     return r;
 }
 __device__ __forceinline__ uint32_t ld_w(const uint32_t* p) {
     uint32_t r;
-    asm("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
+    asm volatile("ld.global.nc.L1::no_allocate.u32 %0, [%1];" : "=r"(r) : "l"(p));
     return r;
 }
 
+// One id at index i of an edge list of Id.
+template <class Id>
+__device__ __forceinline__ uint32_t ld_id(const void* cols, uint64_t i) {
+    if constexpr (sizeof(Id) == 8) return (uint32_t)ld_edge((const uint64_t*)cols + i);
+    else return ld_w((const uint32_t*)cols + i);
+}
+
+// The ids at [j, j + kPerStep), j a multiple of kPerStep: one 16-byte vector
+// load.
+template <class Id>
+__device__ __forceinline__ void ld_ids(const void* cols, uint64_t j, uint32_t* id) {
+    if constexpr (sizeof(Id) == 8) {
+        const ulonglong2 r = ld_edge2((const uint64_t*)cols + j);
+        id[0] = (uint32_t)r.x;
+        id[1] = (uint32_t)r.y;
+    } else {
+        const uint4 r = ld_u32x4((const uint32_t*)cols + j);
+        id[0] = r.x;
+        id[1] = r.y;
+        id[2] = r.z;
+        id[3] = r.w;
+    }
+}
 // First index the aligned read starts from: the largest index <= s whose
 // address is on a 128-byte boundary (the listing "Coalesced Memory Access
-// (Merged + Aligned)" masks the low four index bits for 8-byte ids; `shift`
-// accounts for an edge list whose base is not itself line aligned).  Never
-// below 0; always even, so 16-byte vector loads stay aligned.
+// (Merged + Aligned)" masks the low index bits: four for 8-byte ids, five
+// for 4-byte ids; `shift` accounts for an edge list whose base is not itself
+// line aligned).  Never below 0; always a multiple of kPerStep, so 16-byte
+// vector loads stay aligned.
+template <class Id = uint64_t>
 __device__ __forceinline__ uint64_t aligned_start(uint64_t s, uint32_t shift) {
-    uint64_t r = (s + shift) & 15u;
+    const uint64_t r = (s + shift) & (uint64_t)(IdWidth<Id>::kPerLine - 1);
     return s >= r ? s - r : 0;
 }
 
@@ -255,7 +307,7 @@ struct MsBfsOp {
     static constexpr S kSkip = 0ull;
     static constexpr bool kWeights = false;
     static constexpr bool kPush = true;
-    static constexpr int kSteps = 1;
+    static constexpr int kSteps = 4;
     __device__ __forceinline__ S begin(uint32_t v) {
         const S f = front[v];
         if (f) front[v] = 0ull;  // each vertex is queued once per sweep
@@ -385,28 +437,40 @@ __device__ __forceinline__ void add_scanned(const Sweep& c, unsigned long long x
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(c.scanned, x);
 }
 
-// One 16-byte step of a list read: the lane covers ids j and j+1 of [s, e).
-// Loading and visiting are split so that a lane can issue several steps'
-// loads before it waits on the first (more 16-byte requests in flight).
+// One 16-byte step of a list read: the lane covers ids [j, j + E) of [s, e),
+// E = kPerStep.  Loading and visiting are split so that a lane can issue
+// several steps' loads before it waits on the first (more 16-byte requests in
+// flight).  The two widths are written out separately (a pair of uint64 ids,
+// a quad of uint32 ids) rather than as loops over E: the loop form compiled
+// to code that was 50 % slower from host memory on GB300 (the largest SSSP
+// sweep 11.8 -> 18.2 ms) with the same loads and updates.
 struct PairLoad {
     ulonglong2 id;
     uint2 w;
     uint32_t valid;  // bit 0: id j, bit 1: id j + 1
 };
+struct QuadLoad {
+    uint4 id;
+    uint4 w;
+    uint32_t valid;  // bit i: id j + i
+};
+template <class Id> struct StepOf { using T = PairLoad; };
+template <> struct StepOf<uint32_t> { using T = QuadLoad; };
 
 template <class Op>
 __device__ __forceinline__ PairLoad load_pair(const Sweep& c, uint64_t j, uint64_t s, uint64_t e, bool active) {
+    const uint64_t* cols = (const uint64_t*)c.cols;
     PairLoad p;
     p.id = make_ulonglong2(0, 0);
     p.w = make_uint2(0, 0);
     p.valid = 0;
     if (active && j + 1 >= s) {
         if (j + 1 < e) {
-            p.id = ld_edge2(c.cols + j);
+            p.id = ld_edge2(cols + j);
             if (Op::kWeights) p.w = ld_w2(c.w + j);
             p.valid = (j >= s ? 1u : 0u) | 2u;
         } else if (j < e && j >= s) {
-            p.id.x = ld_edge(c.cols + j);
+            p.id.x = ld_edge(cols + j);
             if (Op::kWeights) p.w.x = ld_w(c.w + j);
             p.valid = 1u;
         }
@@ -414,11 +478,51 @@ __device__ __forceinline__ PairLoad load_pair(const Sweep& c, uint64_t j, uint64
     return p;
 }
 
-// The neighbours' current values (level, distance) a pair's updates compare
+template <class Op>
+__device__ __forceinline__ QuadLoad load_quad(const Sweep& c, uint64_t j, uint64_t s, uint64_t e, bool active) {
+    const uint32_t* cols = (const uint32_t*)c.cols;
+    QuadLoad p;
+    p.id = make_uint4(0, 0, 0, 0);
+    p.w = make_uint4(0, 0, 0, 0);
+    p.valid = 0;
+    if (active && j + 3 >= s && j < e) {
+        if (j + 3 < e) {
+            p.id = ld_u32x4(cols + j);
+            if (Op::kWeights) p.w = ld_u32x4(c.w + j);
+            p.valid = (j >= s ? 1u : 0u) | (j + 1 >= s ? 2u : 0u) | (j + 2 >= s ? 4u : 0u) | 8u;
+        } else {  // the list's last step: element loads, nothing read past e
+            if (j >= s) {
+                p.id.x = ld_w(cols + j);
+                if (Op::kWeights) p.w.x = ld_w(c.w + j);
+                p.valid |= 1u;
+            }
+            if (j + 1 >= s && j + 1 < e) {
+                p.id.y = ld_w(cols + j + 1);
+                if (Op::kWeights) p.w.y = ld_w(c.w + j + 1);
+                p.valid |= 2u;
+            }
+            if (j + 2 >= s && j + 2 < e) {
+                p.id.z = ld_w(cols + j + 2);
+                if (Op::kWeights) p.w.z = ld_w(c.w + j + 2);
+                p.valid |= 4u;
+            }
+        }
+    }
+    return p;
+}
+
+template <class Op, class Id>
+__device__ __forceinline__ typename StepOf<Id>::T load_step(const Sweep& c, uint64_t j, uint64_t s, uint64_t e,
+                                                             bool active) {
+    if constexpr (sizeof(Id) == 8) return load_pair<Op>(c, j, s, e, active);
+    else return load_quad<Op>(c, j, s, e, active);
+}
+
+// The neighbours' current values (level, distance) a step's updates compare
 // against, read before any update so that all of a lane's reads are in
 // flight together rather than one after another.
 template <class Op>
-__device__ __forceinline__ uint2 peek_pair(const Op& op, const PairLoad& p) {
+__device__ __forceinline__ uint2 peek_step(const Op& op, const PairLoad& p) {
     uint2 cur = make_uint2(0, 0);
     if (Op::kPeek) {
         if (p.valid & 1u) cur.x = op.peek(p.id.x);
@@ -426,44 +530,118 @@ __device__ __forceinline__ uint2 peek_pair(const Op& op, const PairLoad& p) {
     }
     return cur;
 }
+template <class Op>
+__device__ __forceinline__ uint4 peek_step(const Op& op, const QuadLoad& p) {
+    uint4 cur = make_uint4(0, 0, 0, 0);
+    if (Op::kPeek) {
+        if (p.valid & 1u) cur.x = op.peek(p.id.x);
+        if (p.valid & 2u) cur.y = op.peek(p.id.y);
+        if (p.valid & 4u) cur.z = op.peek(p.id.z);
+        if (p.valid & 8u) cur.w = op.peek(p.id.w);
+    }
+    return cur;
+}
+template <class Id> struct CurOf { using T = uint2; };
+template <> struct CurOf<uint32_t> { using T = uint4; };
 
-// Full-warp append of up to two ids per lane, called where the whole warp is
-// converged: one atomicAdd per warp per call however the lanes diverged in
-// their updates, and each lane's slots from a ballot prefix count.
-__device__ __forceinline__ void warp_push2(uint32_t* q, uint32_t* count, bool p0, uint32_t id0, bool p1,
-                                           uint32_t id1) {
-    const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
-    const uint32_t total = __popc(b0) + __popc(b1);
-    if (total == 0) return;
+// Per-warp staging of queue appends in shared memory: a warp collects the ids
+// it pushes and appends them to the global queue with one atomicAdd (and one
+// coalesced copy) per buffer, instead of one atomicAdd per warp and step on
+// the single queue counter, which every warp of a dense level contends for.
+constexpr int kWarpBuf = 256;
+struct WarpQ {
+    uint32_t* buf;  // this warp's kWarpBuf entries of shared memory
+    uint32_t cnt;   // entries held (the same in every lane)
+};
+
+// Appends the held entries (whole warp, converged).
+__device__ __forceinline__ void warpq_flush(WarpQ& wq, uint32_t* q, uint32_t* count) {
+    if (wq.cnt == 0) return;
     const int lane = threadIdx.x & 31;
     uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(count, total);
+    if (lane == 0) base = atomicAdd(count, wq.cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
-    const unsigned below = (1u << lane) - 1u;
-    if (p0) q[base + __popc(b0 & below)] = id0;
-    if (p1) q[base + __popc(b0) + __popc(b1 & below)] = id1;
+    __syncwarp();
+    for (uint32_t i = lane; i < wq.cnt; i += 32) q[base + i] = wq.buf[i];
+    __syncwarp();
+    wq.cnt = 0;
+}
+
+// Stages up to four ids per lane (whole warp, converged); the slots come from
+// ballot prefix counts.
+__device__ __forceinline__ void warpq_push4(WarpQ& wq, uint32_t* q, uint32_t* count, bool p0, bool p1, bool p2,
+                                            bool p3, uint4 id) {
+    const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
+    const unsigned b2 = __ballot_sync(0xffffffffu, p2), b3 = __ballot_sync(0xffffffffu, p3);
+    const uint32_t n0 = __popc(b0), n1 = __popc(b1), n2 = __popc(b2);
+    const uint32_t total = n0 + n1 + n2 + __popc(b3);
+    if (total == 0) return;
+    if (wq.cnt + total > (uint32_t)kWarpBuf) warpq_flush(wq, q, count);
+    const unsigned below = (1u << (threadIdx.x & 31)) - 1u;
+    uint32_t* b = wq.buf + wq.cnt;
+    if (p0) b[__popc(b0 & below)] = id.x;
+    if (p1) b[n0 + __popc(b1 & below)] = id.y;
+    if (p2) b[n0 + n1 + __popc(b2 & below)] = id.z;
+    if (p3) b[n0 + n1 + n2 + __popc(b3 & below)] = id.w;
+    wq.cnt += total;
 }
 
 template <class Op>
-__device__ __forceinline__ void visit_pair(const Sweep& c, Op& op, typename Op::S st, uint32_t v, const PairLoad& p,
-                                           uint2 cur) {
+__device__ __forceinline__ void visit_step(const Sweep& c, Op& op, typename Op::S st, uint32_t v, const PairLoad& p,
+                                           uint2 cur, WarpQ& wq) {
     const bool p0 = (p.valid & 1u) && op.visit(st, v, p.id.x, p.w.x, cur.x);
     const bool p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y, cur.y);
-    if (Op::kPush) warp_push2(c.out_q, c.out_count, p0, (uint32_t)p.id.x, p1, (uint32_t)p.id.y);
+    if (Op::kPush)
+        warpq_push4(wq, c.out_q, c.out_count, p0, p1, false, false,
+                    make_uint4((uint32_t)p.id.x, (uint32_t)p.id.y, 0u, 0u));
+}
+template <class Op>
+__device__ __forceinline__ void visit_step(const Sweep& c, Op& op, typename Op::S st, uint32_t v, const QuadLoad& p,
+                                           uint4 cur, WarpQ& wq) {
+    const bool p0 = (p.valid & 1u) && op.visit(st, v, p.id.x, p.w.x, cur.x);
+    const bool p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y, cur.y);
+    const bool p2 = (p.valid & 4u) && op.visit(st, v, p.id.z, p.w.z, cur.z);
+    const bool p3 = (p.valid & 8u) && op.visit(st, v, p.id.w, p.w.w, cur.w);
+    if (Op::kPush) warpq_push4(wq, c.out_q, c.out_count, p0, p1, p2, p3, p.id);
+}
+
+// Shared-memory staging buffers of the (at most 8) warps of a 256-thread block.
+template <class Op>
+__device__ __forceinline__ WarpQ warpq_begin() {
+    __shared__ uint32_t bufs[Op::kPush ? 8 * kWarpBuf : 1];
+    WarpQ wq;
+    wq.buf = bufs + (Op::kPush ? (threadIdx.x >> 5) * kWarpBuf : 0);
+    wq.cnt = 0;
+    return wq;
 }
 
 // Steps whose loads (and neighbour reads) a lane issues back to back before
-// it updates any neighbour: Op::kSteps.  Measured on GB300 (uniform degree-32
-// graph): 4 helps top-down BFS from HBM (8.5 -> 7.6 ms) and changes nothing
-// from host memory; for SSSP and CC more steps only cost registers
-// (SSSP: 46 -> 91 registers, 5 -> 2 blocks per SM).
+// it updates any neighbour: Op::kSteps.  Measured on GB300: 4 helps top-down
+// BFS from HBM (uniform degree 32: 8.5 -> 7.6 ms) and the 64-source BFS from
+// host memory (Kronecker scale 24: 199 -> 88 ms); for SSSP and CC more steps
+// only cost registers (SSSP: 46 -> 91 registers, 5 -> 2 blocks per SM).
+
+// With 4-byte ids a step carries twice the ids, so the same ids in flight
+// take half the steps: batches of Op::kSteps / EMOGI_IDS32_STEP_DIV steps
+// (measured on GB300, uniform degree 32 from host memory: BFS 3.7 -> 3.4 ms
+// with 2 instead of 4 steps of four ids).
+#ifndef EMOGI_IDS32_STEP_DIV
+#define EMOGI_IDS32_STEP_DIV 2
+#endif
+template <class Op, class Id>
+constexpr int batch_steps() {
+    return (IdWidth<Id>::kPerStep == 4 && Op::kSteps >= EMOGI_IDS32_STEP_DIV) ? Op::kSteps / EMOGI_IDS32_STEP_DIV
+                                                                               : Op::kSteps;
+}
 
 // ------------------------------------------------------------------ kernels
 // Merged + aligned expansion with G lanes per vertex (G = 4, 8, 16, 32).
 // Loops are warp-uniform: a warp runs as many steps as its longest group.
-template <class Op, int G>
+template <class Op, int G, class Id = uint64_t>
 __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
-    constexpr int GPW = 32 / G;
+    constexpr int GPW = 32 / G, E = IdWidth<Id>::kPerStep, LINE = IdWidth<Id>::kPerLine;
+    constexpr int KS = batch_steps<Op, Id>();
+    WarpQ wq = warpq_begin<Op>();
     const uint32_t lane = threadIdx.x & 31u, glane = lane % G, grp = lane / G;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -483,42 +661,46 @@ __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
             s = c.off[v];
             e = c.off[v + 1];
         }
-        uint64_t a = aligned_start(s, c.shift);
-        const uint64_t lines = e > s ? (e - a + 15) >> 4 : 0;
+        uint64_t a = aligned_start<Id>(s, c.shift);
+        const uint64_t lines = e > s ? (e - a + LINE - 1) / LINE : 0;
         if (glane == 0) scanned += e - s;
         if (lines > c.large_lines) {
             if (glane == 0) defer(c, v, (lines + c.chunk_lines - 1) / c.chunk_lines, (unsigned long long)st);
             s = e = a = 0;
         }
-        const uint32_t steps = e > s ? (uint32_t)((e - a + 2 * G - 1) / (2 * G)) : 0u;
+        const uint32_t steps = e > s ? (uint32_t)((e - a + E * G - 1) / (E * G)) : 0u;
         const uint32_t maxsteps = __reduce_max_sync(0xffffffffu, steps);
-        for (uint32_t t0 = 0; t0 < maxsteps; t0 += Op::kSteps) {
-            PairLoad p[Op::kSteps];
-            uint2 cur[Op::kSteps];
+        for (uint32_t t0 = 0; t0 < maxsteps; t0 += KS) {
+            typename StepOf<Id>::T p[KS];
+            typename CurOf<Id>::T cur[KS];
 #pragma unroll
-            for (int u = 0; u < Op::kSteps; u++)
-                p[u] = load_pair<Op>(c, a + (uint64_t)(t0 + u) * (2 * G) + 2 * glane, s, e, t0 + u < steps);
+            for (int u = 0; u < KS; u++)
+                p[u] = load_step<Op, Id>(c, a + (uint64_t)(t0 + u) * (E * G) + E * glane, s, e, t0 + u < steps);
 #pragma unroll
-            for (int u = 0; u < Op::kSteps; u++) cur[u] = peek_pair(op, p[u]);
+            for (int u = 0; u < KS; u++) cur[u] = peek_step(op, p[u]);
 #pragma unroll
-            for (int u = 0; u < Op::kSteps; u++) visit_pair(c, op, st, v, p[u], cur[u]);
+            for (int u = 0; u < KS; u++) visit_step(c, op, st, v, p[u], cur[u], wq);
         }
     }
+    if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count);
     add_scanned(c, scanned);
     op.flush();
 }
 
-template <class Op, int G>
+template <class Op, int G, class Id = uint64_t>
 __global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op_in) {
     Op op = op_in;
-    expand_group_body<Op, G>(c, op);
+    expand_group_body<Op, G, Id>(c, op);
 }
 
 // Split lists: work item i of vertex lq_v[slot] covers lines
 // [i * chunk_lines, (i + 1) * chunk_lines) of its aligned list; one warp per
 // item, 16 bytes per lane (four 128-byte lines per step).
-template <class Op>
+template <class Op, class Id = uint64_t>
 __device__ __forceinline__ void expand_split_body(const Sweep& c, Op& op) {
+    constexpr int E = IdWidth<Id>::kPerStep, LINE = IdWidth<Id>::kPerLine;
+    constexpr int KS = batch_steps<Op, Id>();
+    WarpQ wq = warpq_begin<Op>();
     const uint32_t lane = threadIdx.x & 31u;
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -534,29 +716,30 @@ __device__ __forceinline__ void expand_split_body(const Sweep& c, Op& op) {
         const uint32_t v = c.lq_v[lo];
         const unsigned long long ci = item - c.lq_base[lo];
         const uint64_t s = c.off[v], e = c.off[v + 1];
-        const uint64_t a = aligned_start(s, c.shift);
-        const uint64_t cs = a + ci * 16ull * c.chunk_lines;
-        uint64_t ce = cs + 16ull * c.chunk_lines;
+        const uint64_t a = aligned_start<Id>(s, c.shift);
+        const uint64_t cs = a + ci * (uint64_t)LINE * c.chunk_lines;
+        uint64_t ce = cs + (uint64_t)LINE * c.chunk_lines;
         if (ce > e) ce = e;
         const typename Op::S st = (typename Op::S)c.lq_state[lo];
-        for (uint64_t j0 = cs; j0 < ce; j0 += 64 * Op::kSteps) {
-            PairLoad p[Op::kSteps];
-            uint2 cur[Op::kSteps];
+        for (uint64_t j0 = cs; j0 < ce; j0 += 32 * E * KS) {
+            typename StepOf<Id>::T p[KS];
+            typename CurOf<Id>::T cur[KS];
 #pragma unroll
-            for (int u = 0; u < Op::kSteps; u++) p[u] = load_pair<Op>(c, j0 + 64 * u + 2 * lane, s, ce, true);
+            for (int u = 0; u < KS; u++) p[u] = load_step<Op, Id>(c, j0 + 32 * E * u + E * lane, s, ce, true);
 #pragma unroll
-            for (int u = 0; u < Op::kSteps; u++) cur[u] = peek_pair(op, p[u]);
+            for (int u = 0; u < KS; u++) cur[u] = peek_step(op, p[u]);
 #pragma unroll
-            for (int u = 0; u < Op::kSteps; u++) visit_pair(c, op, st, v, p[u], cur[u]);
+            for (int u = 0; u < KS; u++) visit_step(c, op, st, v, p[u], cur[u], wq);
         }
     }
+    if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count);
     op.flush();
 }
 
-template <class Op>
+template <class Op, class Id = uint64_t>
 __global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op_in) {
     Op op = op_in;
-    expand_split_body<Op>(c, op);
+    expand_split_body<Op, Id>(c, op);
 }
 
 // Bottom-up BFS sweep (the pull direction of direction-optimising BFS, Beamer,
@@ -567,10 +750,10 @@ __global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op_in) {
 // small prefix of few lists instead of every list of a huge frontier.
 // Only the owner writes level[v], and a vertex set to L + 1 during this sweep
 // never reads as L, so plain accesses suffice.
-template <int G>
+template <int G, class Id = uint64_t>
 __global__ void __launch_bounds__(256) k_bfs_bottom_up(Sweep c, uint32_t* level, uint32_t L,
                                                        unsigned long long* fedges) {
-    constexpr int GPW = 32 / G;
+    constexpr int GPW = 32 / G, E = IdWidth<Id>::kPerStep;
     const uint32_t lane = threadIdx.x & 31u, glane = lane % G, grp = lane / G;
     const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << G) - 1u)) << (grp * G);
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -595,20 +778,26 @@ __global__ void __launch_bounds__(256) k_bfs_bottom_up(Sweep c, uint32_t* level,
             found = (hits & gmask) != 0;
             s = s + kHeads < e ? s + kHeads : e;
         }
-        const uint64_t a = aligned_start(s, c.shift);
-        const uint32_t steps = e > s ? (uint32_t)((e - a + 2 * G - 1) / (2 * G)) : 0u;
+        const uint64_t a = aligned_start<Id>(s, c.shift);
+        const uint32_t steps = e > s ? (uint32_t)((e - a + E * G - 1) / (E * G)) : 0u;
         for (uint32_t t = 0; __any_sync(0xffffffffu, t < steps && !found); t++) {
             bool hit = false;
             if (t < steps && !found) {
-                const uint64_t j = a + (uint64_t)t * (2 * G) + 2 * glane;
-                if (j + 1 >= s) {
-                    if (j + 1 < e) {
-                        const ulonglong2 pr = ld_edge2(c.cols + j);
-                        hit = (j >= s && level[(uint32_t)pr.x] == L) || level[(uint32_t)pr.y] == L;
-                        scanned += (j >= s) ? 2 : 1;
-                    } else if (j < e && j >= s) {
-                        hit = level[(uint32_t)ld_edge(c.cols + j)] == L;
-                        scanned += 1;
+                const uint64_t j = a + (uint64_t)t * (E * G) + E * glane;
+                if (j + E - 1 >= s && j < e) {
+                    uint32_t id[E];
+                    if (j + E - 1 < e) {
+                        ld_ids<Id>(c.cols, j, id);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < E; i++) id[i] = (j + i < e) ? ld_id<Id>(c.cols, j + i) : 0u;
+                    }
+#pragma unroll
+                    for (int i = 0; i < E; i++) {
+                        if (j + i >= s && j + i < e) {
+                            hit = hit || level[id[i]] == L;
+                            scanned += 1;
+                        }
                     }
                 }
             }
@@ -628,7 +817,7 @@ __global__ void __launch_bounds__(256) k_bfs_bottom_up(Sweep c, uint32_t* level,
 
 // The paper's "Merged" variant: one warp per vertex, lanes read consecutive
 // 8-byte entries starting at the list's own first element.
-template <class Op>
+template <class Op, class Id = uint64_t>
 __global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op_in) {
     Op op = op_in;
     const uint32_t lane = threadIdx.x & 31u;
@@ -645,7 +834,7 @@ __global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op_in) {
         const uint64_t s = c.off[v], e = c.off[v + 1];
         if (lane == 0) scanned += e - s;
         for (uint64_t i = s + lane; i < e; i += 32) {
-            const uint64_t u = ld_edge(c.cols + i);
+            const uint32_t u = ld_id<Id>(c.cols, i);
             const uint32_t w = Op::kWeights ? ld_w(c.w + i) : 0u;
             if (op.visit(st, v, u, w, Op::kPeek ? op.peek(u) : 0u) && Op::kPush)
                 push(c.out_q, c.out_count, (uint32_t)u);
@@ -657,7 +846,7 @@ __global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op_in) {
 }
 
 // The paper's "Naive" variant: one thread per vertex, element by element.
-template <class Op>
+template <class Op, class Id = uint64_t>
 __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
     Op op = op_in;
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -671,7 +860,7 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
         const uint64_t s = c.off[v], e = c.off[v + 1];
         scanned += e - s;
         for (uint64_t i = s; i < e; i++) {
-            const uint64_t u = ld_edge(c.cols + i);
+            const uint32_t u = ld_id<Id>(c.cols, i);
             const uint32_t w = Op::kWeights ? ld_w(c.w + i) : 0u;
             if (op.visit(st, v, u, w, Op::kPeek ? op.peek(u) : 0u) && Op::kPush)
                 push(c.out_q, c.out_count, (uint32_t)u);
@@ -682,14 +871,57 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
     op.flush();
 }
 
+// Block-aggregated queue append for kernels whose blocks step through the
+// vertex range together: a block collects the ids its threads push in shared
+// memory and appends them with one atomicAdd per kBlockBuf/2 ids or so,
+// instead of one per warp and pass (every warp of a dense scan pushes, so
+// per-warp appends meet on the one queue counter).
+constexpr int kBlockBuf = 2048;
+struct BlockQueue {
+    uint32_t ids[kBlockBuf];
+    uint32_t count;
+    uint32_t base;
+};
+
+// Appends the buffered ids (whole block, converged).
+__device__ __forceinline__ void block_queue_flush(BlockQueue& bq, uint32_t* q, uint32_t* qcount) {
+    __syncthreads();
+    const uint32_t k = bq.count;
+    if (threadIdx.x == 0 && k) bq.base = atomicAdd(qcount, k);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) q[bq.base + i] = bq.ids[i];
+    __syncthreads();
+    if (threadIdx.x == 0) bq.count = 0;
+    __syncthreads();
+}
+
+// Adds this thread's id if `p` (whole block, converged); flushes first when
+// one more pass of the block might not fit.
+__device__ __forceinline__ void block_queue_push(BlockQueue& bq, uint32_t* q, uint32_t* qcount, bool p,
+                                                 uint32_t id) {
+    const unsigned b = __ballot_sync(0xffffffffu, p);
+    const int lane = threadIdx.x & 31;
+    uint32_t slot = 0;
+    if (lane == 0 && b) slot = atomicAdd(&bq.count, (uint32_t)__popc(b));  // shared-memory atomic
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    if (p) bq.ids[slot + __popc(b & ((1u << lane) - 1u))] = id;
+    __syncthreads();
+    const uint32_t cnt = bq.count;
+    __syncthreads();  // every thread has read the count before the next pass adds to it
+    if (cnt + blockDim.x > (uint32_t)kBlockBuf) block_queue_flush(bq, q, qcount);
+}
+
 __device__ __forceinline__ void far_split_body(uint32_t n, uint32_t* fflag, const uint32_t* dist, const uint32_t* xd,
                                                uint32_t* qround, uint32_t T, uint32_t round, uint32_t* nq_out,
                                                uint32_t* ncount_out, uint32_t* kept, uint32_t* far_min) {
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    __shared__ BlockQueue bq;
+    if (threadIdx.x == 0) bq.count = 0;
+    __syncthreads();
     uint32_t lmin = INF, lkept = 0;
-    for (uint64_t base = tid - (threadIdx.x & 31); base < n; base += nt) {
-        const uint64_t v = base + (threadIdx.x & 31);
+    // every thread of a block runs the same number of passes (the bound is per block)
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t v = base + threadIdx.x;
+        bool near = false;
         if (v < n && fflag[v]) {
             const uint32_t d = dist[v];
             if (d >= xd[v]) {
@@ -697,13 +929,15 @@ __device__ __forceinline__ void far_split_body(uint32_t n, uint32_t* fflag, cons
             } else if (d < T) {
                 fflag[v] = 0u;
                 qround[v] = round;  // queued for the next sweep
-                push(nq_out, ncount_out, (uint32_t)v);
+                near = true;
             } else {
                 lmin = d < lmin ? d : lmin;
                 lkept++;
             }
         }
+        block_queue_push(bq, nq_out, ncount_out, near, (uint32_t)v);
     }
+    block_queue_flush(bq, nq_out, ncount_out);
     warp_atomic_min(far_min, lmin);
     const uint32_t wk = __reduce_add_sync(0xffffffffu, lkept);
     if ((threadIdx.x & 31) == 0 && wk) atomicAdd(kept, wk);
@@ -761,24 +995,24 @@ __device__ __forceinline__ void sssp_loop_views(const SsspFixed& f, const SsspLo
     *op = SsspOp{L.dist, f.qround, f.fflag, f.xd, &ctr->far_min, &ctr->overflow, L.T, L.sweeps, INF};
 }
 
-template <class Ctr, int G>
+template <class Ctr, int G, class Id>
 __global__ void __launch_bounds__(256) k_sssp_loop_sweep(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
     const SsspLoop L = *Lp;
     if (L.mode != 0) return;
     Sweep s;
     SsspOp op;
     sssp_loop_views(f, L, ctr, &s, &op);
-    expand_group_body<SsspOp, G>(s, op);
+    expand_group_body<SsspOp, G, Id>(s, op);
 }
 
-template <class Ctr>
+template <class Ctr, class Id>
 __global__ void __launch_bounds__(256) k_sssp_loop_lists(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
     const SsspLoop L = *Lp;
     if (L.mode != 0) return;
     Sweep s;
     SsspOp op;
     sssp_loop_views(f, L, ctr, &s, &op);
-    expand_split_body<SsspOp>(s, op);
+    expand_split_body<SsspOp, Id>(s, op);
 }
 
 template <class Ctr>
@@ -940,8 +1174,9 @@ static __global__ void k_ms_reached_edges(const unsigned long long* visit, const
 
 // Sampled CC, first phase: every vertex is linked with its first `rounds`
 // neighbours (one or two ids, usually one 32-byte sector of the edge list).
-static __global__ void k_cc_sample(const uint64_t* off, const uint64_t* cols, const uint32_t* heads, uint32_t* parent,
-                                   uint32_t n, uint32_t rounds, unsigned long long* scanned) {
+template <class Id>
+__global__ void k_cc_sample(const uint64_t* off, const void* cols, const uint32_t* heads, uint32_t* parent,
+                            uint32_t n, uint32_t rounds, unsigned long long* scanned) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     unsigned long long cnt = 0;
@@ -952,7 +1187,7 @@ static __global__ void k_cc_sample(const uint64_t* off, const uint64_t* cols, co
             for (uint64_t r = 0; r < k; r++) uf_union(parent, (uint32_t)v, heads[v * kHeads + r]);
             continue;
         }
-        for (uint64_t r = 0; r < k; r++) uf_union(parent, (uint32_t)v, (uint32_t)ld_edge(cols + s + r));
+        for (uint64_t r = 0; r < k; r++) uf_union(parent, (uint32_t)v, ld_id<Id>(cols, s + r));
         cnt += k;
     }
 #pragma unroll

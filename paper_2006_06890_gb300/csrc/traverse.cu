@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -116,29 +117,29 @@ Sweep make_sweep(const Ctx& c, int side, bool all_vertices) {
 
 // One sweep over k active vertices: the neighbour expansion of the chosen
 // access variant (plus the split-list pass for MERGED_ALIGNED).
-template <class Op>
-emogi_status sweep(Ctx& c, const Sweep& s, const Op& op, uint64_t k) {
+template <class Op, class Id>
+emogi_status sweep_ids(Ctx& c, const Sweep& s, const Op& op, uint64_t k) {
     Workspace& ws = c.g->ws;
     const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
     if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
     switch (c.o.access) {
         case EMOGI_ACCESS_NAIVE:
-            dev::k_expand_naive<Op><<<grid_for(c, k), kThreads, 0, c.st>>>(s, op);
+            dev::k_expand_naive<Op, Id><<<grid_for(c, k), kThreads, 0, c.st>>>(s, op);
             c.kernel_launches += 1;
             break;
         case EMOGI_ACCESS_MERGED:
-            dev::k_expand_merged<Op><<<grid_for(c, k * 32), kThreads, 0, c.st>>>(s, op);
+            dev::k_expand_merged<Op, Id><<<grid_for(c, k * 32), kThreads, 0, c.st>>>(s, op);
             c.kernel_launches += 1;
             break;
         default: {
             const int grid = grid_for(c, k * c.G);
             switch (c.G) {
-                case 4: dev::k_expand_group<Op, 4><<<grid, kThreads, 0, c.st>>>(s, op); break;
-                case 8: dev::k_expand_group<Op, 8><<<grid, kThreads, 0, c.st>>>(s, op); break;
-                case 16: dev::k_expand_group<Op, 16><<<grid, kThreads, 0, c.st>>>(s, op); break;
-                default: dev::k_expand_group<Op, 32><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                case 4: dev::k_expand_group<Op, 4, Id><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                case 8: dev::k_expand_group<Op, 8, Id><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                case 16: dev::k_expand_group<Op, 16, Id><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                default: dev::k_expand_group<Op, 32, Id><<<grid, kThreads, 0, c.st>>>(s, op); break;
             }
-            dev::k_expand_split<Op><<<c.sms * 4, kThreads, 0, c.st>>>(s, op);
+            dev::k_expand_split<Op, Id><<<c.sms * 4, kThreads, 0, c.st>>>(s, op);
             c.kernel_launches += 2;
         }
     }
@@ -148,8 +149,14 @@ emogi_status sweep(Ctx& c, const Sweep& s, const Op& op, uint64_t k) {
     return EMOGI_OK;
 }
 
+template <class Op>
+emogi_status sweep(Ctx& c, const Sweep& s, const Op& op, uint64_t k) {
+    return c.g->id_bytes == 4 ? sweep_ids<Op, uint32_t>(c, s, op, k) : sweep_ids<Op, uint64_t>(c, s, op, k);
+}
+
 // One bottom-up BFS sweep over all vertices at level L.
-emogi_status sweep_bottom_up(Ctx& c, const Sweep& s, uint32_t* level, uint32_t L) {
+template <class Id>
+emogi_status sweep_bottom_up_ids(Ctx& c, const Sweep& s, uint32_t* level, uint32_t L) {
     Workspace& ws = c.g->ws;
     const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
     if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
@@ -157,14 +164,19 @@ emogi_status sweep_bottom_up(Ctx& c, const Sweep& s, uint32_t* level, uint32_t L
     const int grid = grid_for(c, (uint64_t)c.g->n * G);
     unsigned long long* fe = &ws.ctr->fedges;
     switch (G) {
-        case 4: dev::k_bfs_bottom_up<4><<<grid, kThreads, 0, c.st>>>(s, level, L, fe); break;
-        default: dev::k_bfs_bottom_up<8><<<grid, kThreads, 0, c.st>>>(s, level, L, fe); break;
+        case 4: dev::k_bfs_bottom_up<4, Id><<<grid, kThreads, 0, c.st>>>(s, level, L, fe); break;
+        default: dev::k_bfs_bottom_up<8, Id><<<grid, kThreads, 0, c.st>>>(s, level, L, fe); break;
     }
     EMOGI_CUDA_TRY(cudaGetLastError());
     if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[3], c.st));
     c.kernel_launches++;
     c.expand_launches++;
     return EMOGI_OK;
+}
+
+emogi_status sweep_bottom_up(Ctx& c, const Sweep& s, uint32_t* level, uint32_t L) {
+    return c.g->id_bytes == 4 ? sweep_bottom_up_ids<uint32_t>(c, s, level, L)
+                              : sweep_bottom_up_ids<uint64_t>(c, s, level, L);
 }
 
 emogi_status read_counters(Ctx& c, bool after_sweep = true) {
@@ -214,7 +226,7 @@ emogi_status finish(Ctx& c, uint32_t* state, uint32_t* out, bool count_reached, 
         stats->iterations = iterations;
         stats->edges_scanned = ws.h_ctr->scanned;
         stats->edges_reached = count_reached ? ws.h_ctr->reached : g->m;
-        stats->edge_bytes = ws.h_ctr->scanned * 8ull;
+        stats->edge_bytes = ws.h_ctr->scanned * g->id_bytes;
         stats->weight_bytes = weights ? ws.h_ctr->scanned * 4ull : 0;
         stats->ms = ms;
         stats->expand_ms = c.expand_ms;
@@ -246,6 +258,26 @@ emogi_status level_loop(Ctx& c, MakeOp make_op, uint32_t* iterations) {
     return EMOGI_OK;
 }
 
+// Direction of the next BFS level by the list entries each would read (over
+// the host link every entry costs the same, whichever direction reads it).
+// Top-down reads the frontier's lists: mf entries.  Bottom-up reads, for each
+// of the nu unreached vertices, its list up to its first neighbour in the
+// frontier.  A list entry points into the frontier with probability
+// p = mf / m (the frontier's share of edge endpoints), so a vertex of the
+// unreached vertices' mean degree d reads sum_{i<d} (1-p)^i entries, of which
+// the first `heads` come from GPU memory when the list heads are mirrored
+// there; the scan of all n levels adds a fixed cost of about n/32 entries.
+bool bottom_up_reads_less(uint64_t n, uint64_t m, uint64_t mf, uint64_t nu, uint64_t mu, bool heads) {
+    if (mf == 0 || m == 0) return false;
+    if (nu == 0) return (double)n / 32.0 < (double)mf;  // nothing left to find: only the level scan
+    const double p = std::min(1.0, (double)mf / (double)m), q = 1.0 - p;
+    const double d = (double)mu / (double)nu;
+    const double H = heads ? (double)dev::kHeads : 0.0;
+    double per = 0.0;  // link entries per unreached vertex
+    if (p < 1.0 && d > H) per = std::pow(q, H) * (1.0 - std::pow(q, d - H)) / p;
+    return (double)nu * per + (double)n / 32.0 < (double)mf;
+}
+
 emogi_status check_output(emogi_graph g, const Opts& o, void* out) {
     if (!out && g->n) return fail(EMOGI_E_ARG, "output pointer is NULL");
     if (o.out_on_device && out) {
@@ -257,6 +289,18 @@ emogi_status check_output(emogi_graph g, const Opts& o, void* out) {
         }
     }
     return EMOGI_OK;
+}
+
+template <class Id>
+void record_sssp_sweeps(uint32_t G, int big, int lists, cudaStream_t cs, const dev::SsspFixed& f, dev::SsspLoop* L,
+                        DevCounters* ctr) {
+    switch (G) {
+        case 4: dev::k_sssp_loop_sweep<DevCounters, 4, Id><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
+        case 8: dev::k_sssp_loop_sweep<DevCounters, 8, Id><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
+        case 16: dev::k_sssp_loop_sweep<DevCounters, 16, Id><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
+        default: dev::k_sssp_loop_sweep<DevCounters, 32, Id><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
+    }
+    dev::k_sssp_loop_lists<DevCounters, Id><<<lists, kThreads, 0, cs>>>(f, L, ctr);
 }
 
 // Records the device-driven SSSP loop of graph g as a CUDA graph (once per
@@ -298,13 +342,8 @@ emogi_status build_sssp_exec(Ctx& c) {
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const int big = c.sms * 8, lists = c.sms * 4;
-        switch (c.G) {
-            case 4: dev::k_sssp_loop_sweep<DevCounters, 4><<<big, kThreads, 0, cs>>>(f, L, ws.ctr); break;
-            case 8: dev::k_sssp_loop_sweep<DevCounters, 8><<<big, kThreads, 0, cs>>>(f, L, ws.ctr); break;
-            case 16: dev::k_sssp_loop_sweep<DevCounters, 16><<<big, kThreads, 0, cs>>>(f, L, ws.ctr); break;
-            default: dev::k_sssp_loop_sweep<DevCounters, 32><<<big, kThreads, 0, cs>>>(f, L, ws.ctr); break;
-        }
-        dev::k_sssp_loop_lists<DevCounters><<<lists, kThreads, 0, cs>>>(f, L, ws.ctr);
+        if (g->id_bytes == 4) record_sssp_sweeps<uint32_t>(c.G, big, lists, cs, f, L, ws.ctr);
+        else record_sssp_sweeps<uint64_t>(c.G, big, lists, cs, f, L, ws.ctr);
         dev::k_sssp_loop_far<DevCounters><<<big, kThreads, 0, cs>>>(f, L, ws.ctr);
         dev::k_sssp_loop_control<DevCounters><<<1, 1, 0, cs>>>(L, ws.ctr, handle);
         cudaGraph_t captured = body;
@@ -343,20 +382,25 @@ emogi_status emogi_bfs(emogi_graph g, uint64_t src, uint32_t* level, const emogi
                                                                   nullptr, &ws.ctr->qcount[0]);
     EMOGI_CUDA_TRY(cudaGetLastError());
     c.kernel_launches++;
-    // direction choice of Beamer et al.: go bottom-up when the frontier's edges
-    // exceed 1/14 of the unreached vertices' edges, back to top-down when the
-    // frontier holds fewer than n/24 vertices
     const bool diropt = (g->flags & EMOGI_LOAD_UNDIRECTED) && !(c.o.flags & EMOGI_OPT_TOP_DOWN_ONLY) &&
                         c.o.access == EMOGI_ACCESS_MERGED_ALIGNED;
+    const bool beamer = c.o.flags & EMOGI_OPT_BEAMER;
     int side = 0;
-    uint64_t nf = 1, mf = 0, mu = g->m;
+    uint64_t nf = 1, mf = 0, mu = g->m, reached = 1;
     bool top_down = true;
     uint32_t it = 0;
     while (nf > 0) {
         if (it > g->n + 1) return fail(EMOGI_E_TIMEOUT, "BFS did not converge in %u levels", it);
         if (diropt && it > 0) {
-            if (top_down && mf > mu / 14) top_down = false;
-            else if (!top_down && nf < g->n / 24) top_down = true;
+            if (beamer) {
+                // the rule of Beamer et al.: bottom-up when the frontier's edges
+                // exceed 1/14 of the unreached vertices' edges, back to top-down
+                // when the frontier holds fewer than n/24 vertices
+                if (top_down && mf > mu / 14) top_down = false;
+                else if (!top_down && nf < g->n / 24) top_down = true;
+            } else {
+                top_down = !bottom_up_reads_less(g->n, g->m, mf, g->n - reached, mu, g->d_heads != nullptr);
+            }
         }
         EMOGI_TRY(reset_sweep_counters(c, side));
         EMOGI_CUDA_TRY(cudaMemsetAsync(&ws.ctr->fedges, 0, sizeof(unsigned long long), c.st));
@@ -371,6 +415,7 @@ emogi_status emogi_bfs(emogi_graph g, uint64_t src, uint32_t* level, const emogi
         nf = ws.h_ctr->qcount[side ^ 1];
         mf = ws.h_ctr->fedges;
         mu -= std::min(mu, mf);
+        reached += nf;
         side ^= 1;
         it++;
     }
@@ -588,7 +633,7 @@ emogi_status emogi_msbfs(emogi_graph g, const uint64_t* srcs, uint32_t k, uint32
         stats->iterations = it;
         stats->edges_scanned = ws.h_ctr->scanned;
         stats->edges_reached = ws.h_ctr->reached;
-        stats->edge_bytes = ws.h_ctr->scanned * 8ull;
+        stats->edge_bytes = ws.h_ctr->scanned * g->id_bytes;
         stats->ms = ms;
         stats->expand_ms = c.expand_ms;
         stats->expand_launches = c.expand_launches;
@@ -618,8 +663,12 @@ emogi_status emogi_cc(emogi_graph g, uint32_t* label, const emogi_opts* opts, em
         if (sampled) {
             const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
             if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
-            dev::k_cc_sample<<<grid_for(c, n), kThreads, 0, c.st>>>(g->d_off, g->cols, g->d_heads, parent, n, 2,
-                                                                     &ws.ctr->scanned);
+            if (g->id_bytes == 4)
+                dev::k_cc_sample<uint32_t><<<grid_for(c, n), kThreads, 0, c.st>>>(g->d_off, g->cols, g->d_heads,
+                                                                                   parent, n, 2, &ws.ctr->scanned);
+            else
+                dev::k_cc_sample<uint64_t><<<grid_for(c, n), kThreads, 0, c.st>>>(g->d_off, g->cols, g->d_heads,
+                                                                                   parent, n, 2, &ws.ctr->scanned);
             EMOGI_CUDA_TRY(cudaGetLastError());
             if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[3], c.st));
             c.expand_launches++;

@@ -36,6 +36,7 @@ OPT_TIME_KERNELS = 1
 OPT_TOP_DOWN_ONLY = 2
 OPT_CC_FULL_PASS = 4
 OPT_HOST_LOOP = 8
+OPT_BEAMER = 16
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -71,6 +72,7 @@ class Stats(ctypes.Structure):
 _P, _U64, _U32, _I32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
 _SIGNATURES = [
     ("emogi_load_csr", _I32, [_U64, _U64, _P, _P, _P, _I32, _U32, ctypes.POINTER(_P)]),
+    ("emogi_load_csr32", _I32, [_U64, _U64, _P, _P, _P, _I32, _U32, ctypes.POINTER(_P)]),
     ("emogi_bfs", _I32, [_P, _U64, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
     ("emogi_sssp", _I32, [_P, _U64, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
     ("emogi_cc", _I32, [_P, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
@@ -211,9 +213,7 @@ class Graph:
             pass
 
 
-def load_csr(n, m, row_offsets, col_idx, weights=None, placement="host", flags=0,
-             undirected: Optional[bool] = None, borrow: bool = False, heads: bool = True) -> Graph:
-    """emogi_load_csr: copy (or, with borrow, pin in place) a CSR graph."""
+def _load(entry, id_dtype, n, m, row_offsets, col_idx, weights, placement, flags, undirected, borrow, heads):
     place = PLACEMENTS[placement] if isinstance(placement, str) else int(placement)
     f = int(flags)
     if not heads:
@@ -223,27 +223,44 @@ def load_csr(n, m, row_offsets, col_idx, weights=None, placement="host", flags=0
     if borrow:
         f |= LOAD_BORROW
     off = _host_array(row_offsets, np.uint64, "row_offsets")
-    col = _host_array(col_idx, np.uint64, "col_idx")
+    col = _host_array(col_idx, id_dtype, "col_idx")
     w = _host_array(weights, np.uint32, "weights")
     h = ctypes.c_void_p()
-    st = lib().emogi_load_csr(int(n), int(m), off.ctypes.data,
-                              col.ctypes.data if col is not None else None,
-                              w.ctypes.data if w is not None else None,
-                              place, f, ctypes.byref(h))
+    st = getattr(lib(), entry)(int(n), int(m), off.ctypes.data,
+                               col.ctypes.data if col is not None else None,
+                               w.ctypes.data if w is not None else None,
+                               place, f, ctypes.byref(h))
     _check(st)
     keep = (col, w) if (f & LOAD_BORROW) else ()
     return Graph(h.value, int(n), int(m), place, keep)
 
 
-def load_graph(g, placement="host", borrow=False, with_weights=True, heads=True) -> Graph:
-    """Load a graphgen.Graph-like object (n, offsets, cols, weights, undirected)."""
+def load_csr(n, m, row_offsets, col_idx, weights=None, placement="host", flags=0,
+             undirected: Optional[bool] = None, borrow: bool = False, heads: bool = True) -> Graph:
+    """emogi_load_csr: copy (or, with borrow, pin in place) a CSR graph with uint64 ids."""
+    return _load("emogi_load_csr", np.uint64, n, m, row_offsets, col_idx, weights, placement, flags,
+                 undirected, borrow, heads)
+
+
+def load_csr32(n, m, row_offsets, col_idx, weights=None, placement="host", flags=0,
+               undirected: Optional[bool] = None, borrow: bool = False, heads: bool = True) -> Graph:
+    """emogi_load_csr32: as load_csr, with a 4-byte (uint32) edge list."""
+    return _load("emogi_load_csr32", np.uint32, n, m, row_offsets, col_idx, weights, placement, flags,
+                 undirected, borrow, heads)
+
+
+def load_graph(g, placement="host", borrow=False, with_weights=True, heads=True, ids32=False) -> Graph:
+    """Load a graphgen.Graph-like object (n, offsets, cols, weights, undirected);
+    ids32 loads its edge list as uint32 ids (emogi_load_csr32)."""
     w = g.weights if with_weights else None
-    return load_csr(g.n, g.m, g.offsets, g.cols, w, placement=placement,
-                    undirected=bool(getattr(g, "undirected", False)), borrow=borrow, heads=heads)
+    fn = load_csr32 if ids32 else load_csr
+    cols = g.cols.astype(np.uint32) if ids32 else g.cols
+    return fn(g.n, g.m, g.offsets, cols, w, placement=placement,
+              undirected=bool(getattr(g, "undirected", False)), borrow=borrow, heads=heads)
 
 
 def _opts(access=None, granularity=0, chunk_lines=0, timeout_ns=0, stream=None, out_on_device=False,
-          time_kernels=False, delta=0, top_down_only=False, cc_full_pass=False, host_loop=False):
+          time_kernels=False, delta=0, top_down_only=False, cc_full_pass=False, host_loop=False, beamer=False):
     o = Opts()
     o.struct_size = ctypes.sizeof(Opts)
     o.access = ACCESS[access] if isinstance(access, str) else int(access or 0)
@@ -254,7 +271,8 @@ def _opts(access=None, granularity=0, chunk_lines=0, timeout_ns=0, stream=None, 
         o.cuda_stream = int(getattr(stream, "cuda_stream", stream))
     o.out_on_device = 1 if out_on_device else 0
     o.flags = (OPT_TIME_KERNELS if time_kernels else 0) | (OPT_TOP_DOWN_ONLY if top_down_only else 0) | \
-        (OPT_CC_FULL_PASS if cc_full_pass else 0) | (OPT_HOST_LOOP if host_loop else 0)
+        (OPT_CC_FULL_PASS if cc_full_pass else 0) | (OPT_HOST_LOOP if host_loop else 0) | \
+        (OPT_BEAMER if beamer else 0)
     o.delta = int(delta)
     return o
 

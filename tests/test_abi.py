@@ -66,6 +66,22 @@ def test_load_rejects_bad_csr_on_host(E):
     assert e.status == E.E_ARG and "2^32" in str(e)
 
 
+def test_load32_rejects_bad_csr_on_host(E):
+    u, u32 = np.uint64, np.uint32
+
+    def bad(*args, **kw):
+        with pytest.raises(E.EmogiError) as ei:
+            E.load_csr32(*args, **kw)
+        return ei.value
+
+    e = bad(3, 2, np.array([0, 1, 3, 2], dtype=u), np.array([1, 0], dtype=u32))
+    assert e.status == E.E_ARG and "decrease" in str(e)
+    e = bad(3, 2, np.array([0, 1, 2, 2], dtype=u), np.array([1, 3], dtype=u32))
+    assert e.status == E.E_ARG and "col_idx[1] = 3" in str(e)
+    e = bad(2, 2, np.array([0, 1, 2], dtype=u), np.array([1, 0], dtype=u32), placement="managed", borrow=True)
+    assert e.status == E.E_ARG and "BORROW" in str(e)
+
+
 def test_load_rejects_bad_flags_and_placement(E):
     u = np.uint64
     off, col = np.array([0, 1, 2], dtype=u), np.array([1, 0], dtype=u)
