@@ -11,6 +11,7 @@ hand-made graphs come from :func:`csr_from_edges`.
 from __future__ import annotations
 
 import ctypes
+import mmap
 import os
 import subprocess
 from dataclasses import dataclass
@@ -59,10 +60,32 @@ def _ptr(a: Optional[np.ndarray]):
     return None if a is None else ctypes.c_void_p(a.ctypes.data)
 
 
+def _huge_page_bytes() -> int:
+    try:
+        with open("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size") as f:
+            v = int(f.read().strip())
+        return v if v >= 4096 and v & (v - 1) == 0 else 2 << 20
+    except (OSError, ValueError):
+        return 2 << 20
+
+
 def aligned_empty(count: int, dtype, align: int = 4096) -> np.ndarray:
-    """Uninitialised 1-D array whose data pointer is `align`-byte aligned."""
+    """Uninitialised 1-D array whose data pointer is `align`-byte aligned.
+    Arrays of a GiB or more come from an anonymous mapping advised to use
+    transparent huge pages (aligned to the huge-page size), so that a GPU
+    reading them in place (zero-copy) needs few address translations."""
     dtype = np.dtype(dtype)
     nbytes = max(1, int(count)) * dtype.itemsize
+    if nbytes >= (1 << 30) and hasattr(mmap, "MADV_HUGEPAGE"):
+        hp = max(_huge_page_bytes(), align)
+        mm = mmap.mmap(-1, nbytes + hp, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+        raw = np.frombuffer(mm, dtype=np.uint8)
+        off = (-raw.ctypes.data) % hp
+        try:
+            mm.madvise(mmap.MADV_HUGEPAGE, off, nbytes)
+        except (OSError, ValueError):
+            pass  # without transparent huge pages the mapping keeps small pages
+        return raw[off:off + nbytes].view(dtype)[:int(count)]
     raw = np.empty(nbytes + align, dtype=np.uint8)
     off = (-raw.ctypes.data) % align
     return raw[off:off + nbytes].view(dtype)[:int(count)]

@@ -144,6 +144,12 @@ typedef struct {
  * With EMOGI_LOAD_BORROW (HOST only) the library registers col_idx and weights
  * with cudaHostRegister instead of copying; they must be 16-byte aligned and
  * the caller must keep them alive and unchanged until emogi_free_graph.
+ * The GPU reads a borrowed list wherever it lies, so large borrowed arrays
+ * should sit on huge pages (e.g. an anonymous mapping advised with
+ * MADV_HUGEPAGE before it is filled): with 64 KiB pages a 50 GB edge list
+ * needs far more address translations than the GPU holds, and random list
+ * reads then run two orders of magnitude slower.  The library's own HOST
+ * copies of arrays of 1 GiB or more are placed that way.
  * Errors: EMOGI_E_ARG (invalid CSR or flags), EMOGI_E_BUDGET, EMOGI_E_NOMEM,
  * EMOGI_E_CUDA.  On error *out is set to NULL and nothing is retained. */
 emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets,

@@ -249,6 +249,17 @@ __device__ __forceinline__ void warp_atomic_min(uint32_t* out, uint32_t x) {
 //     to the pile.)
 //   xd: the distance v was last expanded with, so a vertex queued twice
 //     (near and far) is not expanded twice with the same distance.
+//   Th: long lists (more than kHeavyEntries entries) are expanded only when
+//     their distance is below Th, the start of the window plus a fraction of
+//     its width; a long-listed vertex of the near frontier at or above Th
+//     goes back to the far pile.  A vertex that many short paths reach
+//     (the hubs of a skewed graph) is improved several times inside a wide
+//     window, and each improvement re-reads its whole list; a narrow window
+//     for long lists only keeps those re-reads rare while short lists keep
+//     the wide window's few rounds.  Measured on GB300, Kronecker scale 24
+//     (hubs of 400 k entries) from host memory: re-expansion 2.49x -> 1.19x,
+//     84 -> 46 ms; no effect on graphs without long lists.
+constexpr uint32_t kHeavyEntries = 512;
 struct SsspOp {
     uint32_t* dist;
     uint32_t* qround;
@@ -259,6 +270,8 @@ struct SsspOp {
     uint32_t T;
     uint32_t round;
     uint32_t lmin;  // per-thread smallest distance sent to the far pile
+    const uint64_t* off = nullptr;  // row offsets (for the list length of a vertex at or above Th)
+    uint32_t Th = INF;
     using S = uint32_t;
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = true;
@@ -267,6 +280,11 @@ struct SsspOp {
     __device__ __forceinline__ S begin(uint32_t v) {
         const uint32_t d = __ldcg(dist + v);
         if (d >= __ldcg(xd + v)) return INF;  // already expanded with this distance
+        if (d >= Th && off[v + 1] - off[v] > kHeavyEntries) {  // a long list waits for a narrower window
+            lmin = d < lmin ? d : lmin;
+            fflag[v] = 1u;
+            return INF;
+        }
         __stcg(xd + v, d);
         return d;
     }
@@ -972,7 +990,15 @@ struct SsspLoop {
     unsigned long long t0, timeout_ns;  // %globaltimer at the first iteration; bound on the loop
     unsigned long long widen, window_work, light, heavy;
     uint32_t* dist;       // this call's distance array
+    uint32_t Th;          // long lists wait while their distance is at or above this
+    uint32_t delta_heavy; // width of the long lists' part of a window
 };
+
+// The long lists' threshold of a window that starts at `lo`.
+__host__ __device__ __forceinline__ uint32_t heavy_threshold(uint64_t lo, uint64_t delta_heavy, uint64_t T) {
+    const uint64_t th = lo + delta_heavy;
+    return (uint32_t)(th < T ? th : T);
+}
 
 // Fixed pointers of one graph's SSSP loop (recorded once in the CUDA graph).
 struct SsspFixed {
@@ -992,7 +1018,8 @@ __device__ __forceinline__ void sssp_loop_views(const SsspFixed& f, const SsspLo
     s->out_q = f.q[L.side ^ 1];
     s->out_count = &ctr->qcount[L.side ^ 1];
     s->large = &ctr->large[0];
-    *op = SsspOp{L.dist, f.qround, f.fflag, f.xd, &ctr->far_min, &ctr->overflow, L.T, L.sweeps, INF};
+    *op = SsspOp{L.dist, f.qround, f.fflag, f.xd, &ctr->far_min, &ctr->overflow, L.T, L.sweeps, INF, f.base.off,
+                 L.Th};
 }
 
 template <class Ctr, int G, class Id>
@@ -1065,6 +1092,7 @@ __global__ void k_sssp_loop_control(SsspLoop* Lp, Ctr* ctr, cudaGraphConditional
         uint64_t Tn = (uint64_t)ctr->far_min + (uint64_t)L.delta * L.widen;
         if (Tn <= L.T) Tn = (uint64_t)L.T + 1;
         L.T = Tn < (uint64_t)INF ? (uint32_t)Tn : INF;
+        L.Th = heavy_threshold(ctr->far_min, L.delta_heavy, L.T);
         ctr->qcount[L.side] = 0;
         ctr->fcount[0] = 0;
         ctr->far_min = INF;

@@ -465,6 +465,8 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         hl->light = EMOGI_SSSP_LIGHT_SHIFT ? std::max<uint64_t>(n >> EMOGI_SSSP_LIGHT_SHIFT, 256) : 0;
         hl->heavy = std::max<uint64_t>(n >> 6, 1);
         hl->dist = state;
+        hl->delta_heavy = (uint32_t)std::max<uint64_t>(std::min<uint64_t>(delta, dev::INF) / 8, 1);
+        hl->Th = dev::heavy_threshold(0, hl->delta_heavy, hl->T);
         // the loop runs on the device: bound it in time as well (the caller's
         // timeout_ns when given, else one minute)
         hl->timeout_ns = (opts && opts->timeout_ns) ? opts->timeout_ns : 60000000000ull;
@@ -495,6 +497,8 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
     // there re-expand only the few vertices they hold.  (A threshold of n/64
     // measured worse on a uniform degree-32 graph: 1.64x re-expansion.)
     uint64_t widen = 1, window_work = 0;
+    const uint64_t delta_heavy = std::max<uint64_t>(std::min<uint64_t>(delta, dev::INF) / 8, 1);
+    uint32_t Th = dev::heavy_threshold(0, delta_heavy, T);
     const uint64_t light = EMOGI_SSSP_LIGHT_SHIFT ? std::max<uint64_t>(n >> EMOGI_SSSP_LIGHT_SHIFT, 256) : 0;
     const uint64_t heavy = std::max<uint64_t>(n >> 6, 1);
     while (nk > 0 || fk > 0) {
@@ -504,7 +508,8 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         if (nk > 0) {
             EMOGI_TRY(reset_sweep_counters(c, side));
             Sweep s = make_sweep(c, side, false);
-            dev::SsspOp op{state, qround, ws.fflag, ws.xd, &ctr->far_min, &ctr->overflow, (uint32_t)T, sweeps, dev::INF};
+            dev::SsspOp op{state,    qround,   ws.fflag, ws.xd, &ctr->far_min, &ctr->overflow, (uint32_t)T, sweeps,
+                           dev::INF, g->d_off, Th};
             EMOGI_TRY(sweep(c, s, op, nk));
             sweeps++;
             window_work += nk;
@@ -521,6 +526,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
             uint64_t Tn = fmin + delta * widen;
             if (Tn <= T) Tn = T + 1;
             T = std::min<uint64_t>(Tn, dev::INF);
+            Th = dev::heavy_threshold(fmin, delta_heavy, T);
             EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->qcount[side], 0, sizeof(uint32_t), c.st));
             EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->fcount[0], 0, sizeof(uint32_t), c.st));
             EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->far_min, 0xFF, sizeof(uint32_t), c.st));
