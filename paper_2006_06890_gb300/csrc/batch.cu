@@ -92,15 +92,38 @@ __device__ bool grid_barrier(BatchCtl* ctl, uint64_t timeout_ns) {
     return ok != 0;
 }
 
-__device__ __forceinline__ void push2(uint2* q, uint32_t* count, uint2 e) {
-    const unsigned mask = __activemask();
+// Per-warp staging of (graph, vertex) appends in shared memory: one
+// atomicAdd and one coalesced copy per buffer instead of one atomicAdd per
+// warp and step on the round's single queue counter.
+constexpr uint32_t kStage = 128;
+struct Stage {
+    uint2* buf;     // this warp's kStage entries
+    uint32_t cnt;   // entries held (the same in every lane)
+};
+
+__device__ __forceinline__ void stage_flush(Stage& st, uint2* q, uint32_t* count) {
+    if (st.cnt == 0) return;
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    const unsigned rank = __popc(mask & ((1u << lane) - 1u));
     uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
-    base = __shfl_sync(mask, base, leader);
-    q[base + rank] = e;
+    if (lane == 0) base = atomicAdd(count, st.cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    __syncwarp();
+    for (uint32_t i = lane; i < st.cnt; i += 32) q[base + i] = st.buf[i];
+    __syncwarp();
+    st.cnt = 0;
+}
+
+// Stages up to two entries per lane (whole warp, converged).
+__device__ __forceinline__ void stage_push2(Stage& st, uint2* q, uint32_t* count, bool p0, uint2 e0, bool p1,
+                                            uint2 e1) {
+    const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
+    const uint32_t n0 = __popc(b0), total = n0 + __popc(b1);
+    if (total == 0) return;
+    if (st.cnt + total > kStage) stage_flush(st, q, count);
+    const unsigned below = (1u << (threadIdx.x & 31)) - 1u;
+    if (p0) st.buf[st.cnt + __popc(b0 & below)] = e0;
+    if (p1) st.buf[st.cnt + n0 + __popc(b1 & below)] = e1;
+    st.cnt += total;
 }
 
 // level[*] = INF for every graph.
@@ -126,6 +149,8 @@ __global__ void __launch_bounds__(256) k_batch_bfs(BatchParams p) {
     constexpr int GPW = 32 / G;
     const uint32_t lane = threadIdx.x & 31u, glane = lane % G, grp = lane / G;
     BatchCtl* ctl = p.ctl;
+    __shared__ uint2 stage_bufs[8 * kStage];
+    Stage stg{stage_bufs + (threadIdx.x >> 5) * kStage, 0u};
     unsigned long long scanned = 0;
     for (uint32_t L = 0;; L++) {
         const uint32_t* in_cnt = &ctl->qcount[L % 3];
@@ -190,17 +215,17 @@ __global__ void __launch_bounds__(256) k_batch_bfs(BatchParams p) {
 #pragma unroll
                     for (int x = 0; x < 2; x++)
                         if (ok[x]) cur[x] = lev[(uint32_t)u[x]];
+                    bool pushed[2] = {false, false};
 #pragma unroll
-                    for (int x = 0; x < 2; x++) {
-                        if (ok[x] && cur[x] == dev::INF) {
-                            uint32_t* pl = lev + (uint32_t)u[x];
-                            if (atomicCAS(pl, dev::INF, L + 1) == dev::INF)
-                                push2(out_q, out_cnt, make_uint2(gi, (uint32_t)u[x]));
-                        }
-                    }
+                    for (int x = 0; x < 2; x++)
+                        if (ok[x] && cur[x] == dev::INF)
+                            pushed[x] = atomicCAS(lev + (uint32_t)u[x], dev::INF, L + 1) == dev::INF;
+                    stage_push2(stg, out_q, out_cnt, pushed[0], make_uint2(gi, u[0]), pushed[1],
+                                make_uint2(gi, u[1]));
                 }
             }
         }
+        stage_flush(stg, out_q, out_cnt);
         if (!grid_barrier(ctl, p.timeout_ns)) break;
         const uint32_t next = *(volatile const uint32_t*)out_cnt;
         if (next == 0) {
