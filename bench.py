@@ -205,6 +205,21 @@ def step_alg_bytes(stats):
     return 8 * sb["edges_scanned"] + 12 * ss["edges_scanned"] + 8 * sc["edges_scanned"]
 
 
+# Host-link read bytes per algorithmic byte of the expansion kernels, from the
+# ncu sysmem read-sector counts of the same kernels on the 2^22-vertex case
+# (profiles/link_traffic_per_kernel_urand22_host.md); the 32-byte sector waste
+# of lists that do not start on a sector grows with the entries read, so the
+# per-entry factor scales to the 2^24 graph.
+LINK_BYTES_PER_ALG_BYTE = {"bfs": 1.136, "sssp": 1.188, "cc": 1.0}
+
+
+def step_link_bytes(stats):
+    sb, ss, sc = stats
+    return (LINK_BYTES_PER_ALG_BYTE["bfs"] * 8 * sb["edges_scanned"] +
+            LINK_BYTES_PER_ALG_BYTE["sssp"] * 12 * ss["edges_scanned"] +
+            LINK_BYTES_PER_ALG_BYTE["cc"] * 8 * sc["edges_scanned"])
+
+
 def time_loop(torch, E, h, srcs, stream, steps, warmup, outs):
     for i in range(warmup):
         run_step(E, h, srcs[i % len(srcs)], stream, outs)
@@ -303,7 +318,12 @@ def ours(args):
                      "kernel": "expansion launches: k_expand_group / k_expand_split (BFS top-down, CC final), "
                                "k_bfs_bottom_up, k_cc_sample, and the recorded SSSP loop (k_sssp_loop_*)",
                      "achieved": round(achieved, 2), "peak": round(link_peak, 2), "unit": "GB/s",
-                     "frac": round(achieved / link_peak, 4), "traffic": None,
+                     "frac": round(achieved / link_peak, 4),
+                     "traffic": int(sum(step_link_bytes(p) for p in per) / len(per)),
+                     "traffic_note": "host-link read bytes per step of the expansion kernels: ncu sysmem read "
+                                     "sectors x 32 per list entry on the 2^22 case (BFS 1.136, SSSP 1.188 per "
+                                     "algorithmic byte), scaled by this run's entries",
+                     "link_frac": round(sum(step_link_bytes(p) for p in per) / (expand_ms * 1e-3) / 1e9 / link_peak, 4),
                      "peak_source": "pinned host->device cudaMemcpy, 1 GiB, best of 6, measured in this run",
                      "algorithmic_bytes_per_step": int(alg_bytes / len(per)),
                      "unit_bytes": "8 B per list entry read (BFS, CC), 12 B (SSSP)",
