@@ -549,3 +549,19 @@ def test_list_heads_on_and_off(placement, name):
                 np.testing.assert_array_equal(E.bfs(h, s)[0], oracle.bfs_g(g, s), err_msg=f"heads={heads} src={s}")
                 np.testing.assert_array_equal(E.bfs(h, s, granularity=4)[0], oracle.bfs_g(g, s))
             np.testing.assert_array_equal(E.cc(h)[0], exp_cc, err_msg=f"heads={heads}")
+
+
+@pytest.mark.slow
+def test_host_arrays_of_a_gib_or_more():
+    """An edge list of 1.3 GB takes the huge-page mapping path of the HOST
+    placement (and graphgen allocates it on huge pages, which BORROW then pins
+    in place); results equal the oracle's either way."""
+    g = gg.uniform(1 << 22, 40, seed=11, weights=True)
+    assert g.m * 8 > (1 << 30) and g.m * 4 < (1 << 30)
+    s = int(gg.random_sources(g, 1, seed=5)[0])
+    exp_bfs, exp_sssp, exp_cc = oracle.bfs_g(g, s), oracle.sssp_g(g, s), oracle.cc_g(g)
+    for borrow in (False, True):
+        with E.load_graph(g, placement="host", borrow=borrow) as h:
+            np.testing.assert_array_equal(E.bfs(h, s)[0], exp_bfs)
+            np.testing.assert_array_equal(E.sssp(h, s)[0], exp_sssp)
+            np.testing.assert_array_equal(E.cc(h)[0], exp_cc)
