@@ -92,9 +92,14 @@ enum {
                                           readback per sweep, as the paper's level loop) instead of a
                                           recorded CUDA graph whose conditional loop decides on the
                                           device */
-    EMOGI_OPT_BEAMER = 1u << 4         /* BFS: choose each level's direction by the fixed thresholds
+    EMOGI_OPT_BEAMER = 1u << 4,        /* BFS: choose each level's direction by the fixed thresholds
                                           of Beamer et al. (alpha = 14, beta = 24) instead of the
                                           estimate of list entries each direction would read */
+    EMOGI_OPT_ORDERED_FRONTIER = 1u << 5 /* SSSP: rebuild every near frontier in vertex order (flag
+                                          per vertex, compacted after each sweep), as the library
+                                          does by itself for edge lists (with weights) of 16 GiB or
+                                          more, whose lists read in arrival order span more address
+                                          range than the GPU's translations cover */
 };
 
 /* Per-call options.  Pass NULL for defaults.  struct_size must be

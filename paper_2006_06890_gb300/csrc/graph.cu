@@ -130,6 +130,7 @@ emogi_status ensure_workspace(emogi_graph g) {
         {(void**)&ws.flag, n * 4, "near flags"},
         {(void**)&ws.fflag, n * 4, "far flags"},
         {(void**)&ws.xd, n * 4, "expanded distances"},
+        {(void**)&ws.nflag, (n / 16 + 1) * 16, "next-frontier flags"},
         {(void**)&ws.lq_v, ws.lq_cap * 4, "split-list vertices"},
         {(void**)&ws.lq_base, ws.lq_cap * 8, "split-list chunk bases"},
         {(void**)&ws.lq_state, ws.lq_cap * 8, "split-list states"},
@@ -146,6 +147,7 @@ emogi_status ensure_workspace(emogi_graph g) {
     cudaError_t e = cudaHostAlloc((void**)&ws.h_ctr, sizeof(DevCounters), cudaHostAllocDefault);
     if (e == cudaSuccess) e = cudaMemset(ws.flag, 0, n * 4);
     if (e == cudaSuccess) e = cudaMemset(ws.fflag, 0, n * 4);
+    if (e == cudaSuccess) e = cudaMemset(ws.nflag, 0, (n / 16 + 1) * 16);
     for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&ws.ev[i]);
     if (e != cudaSuccess) {
         release_workspace(g);
@@ -162,6 +164,7 @@ void release_workspace(emogi_graph g) {
     dev_free(ws.flag, ws.n * 4);
     dev_free(ws.fflag, ws.n * 4);
     dev_free(ws.xd, ws.n * 4);
+    dev_free(ws.nflag, (ws.n / 16 + 1) * 16);
     dev_free(ws.lq_v, ws.lq_cap * 4);
     dev_free(ws.lq_base, ws.lq_cap * 8);
     dev_free(ws.lq_state, ws.lq_cap * 8);

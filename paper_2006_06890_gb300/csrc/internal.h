@@ -76,6 +76,7 @@ struct Workspace {
     uint32_t* flag = nullptr;              // SSSP "in near frontier" flags, all zero between calls
     uint32_t* fflag = nullptr;             // SSSP "in the far pile" flags, all zero between calls
     uint32_t* xd = nullptr;                // SSSP distance of the last expansion
+    uint8_t* nflag = nullptr;              // next frontier as one byte per vertex (n rounded up to 16), zero between calls
     bool flags_dirty = false;              // a call ended early and left flags set
     uint32_t* lq_v = nullptr;              // split-list vertices
     unsigned long long* lq_base = nullptr; // first chunk index of each split-list vertex

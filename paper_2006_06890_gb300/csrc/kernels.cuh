@@ -198,16 +198,21 @@ __device__ __forceinline__ void warp_atomic_add(unsigned long long* out, unsigne
 // The compare-and-swap makes exactly one visitor push it.  When `off` is set,
 // the out-degrees of the vertices pushed are summed into `fedges` (the edge
 // count of the next frontier, which picks the direction of the next level).
-struct BfsOp {
+// kBits: the next frontier is a flag byte per vertex (`nflag`) that a
+// compaction turns into the next queue in vertex order (k_compact_flags);
+// otherwise visitors append to the queue directly.
+template <bool kBits>
+struct BfsOpT {
     uint32_t* level;
     uint32_t next;
     const uint64_t* off = nullptr;
     unsigned long long* fedges = nullptr;
     unsigned long long lf = 0;
+    uint8_t* nflag = nullptr;
     using S = uint32_t;
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = false;
-    static constexpr bool kPush = true;
+    static constexpr bool kPush = !kBits;
     static constexpr int kSteps = 4;
     static constexpr bool kPeek = true;
     __device__ __forceinline__ S begin(uint32_t) { return 0; }
@@ -217,12 +222,18 @@ struct BfsOp {
         if (cur != INF) return false;
         if (atomicCAS(p, INF, next) != INF) return false;
         if (off) lf += off[(uint32_t)u + 1] - off[(uint32_t)u];
+        if (kBits) {
+            nflag[(uint32_t)u] = 1;  // the CAS made this visitor the only one
+            return false;
+        }
         return true;
     }
     __device__ __forceinline__ void flush() {
         if (fedges) warp_atomic_add(fedges, lf);
     }
 };
+using BfsOp = BfsOpT<false>;
+using BfsBitsOp = BfsOpT<true>;
 
 // Warp-reduced atomic minimum of a per-thread value (whole warp converged).
 __device__ __forceinline__ void warp_atomic_min(uint32_t* out, uint32_t x) {
@@ -247,6 +258,10 @@ __device__ __forceinline__ void warp_atomic_min(uint32_t* out, uint32_t x) {
 //     plain store; the split kernel scans all flags.  (A queue needed an
 //     atomic exchange plus an append on one shared counter per vertex sent
 //     to the pile.)
+//   nflag: the next near frontier as a flag byte per vertex (a plain store:
+//     the stamp already picked one improver per sweep); after the sweep a
+//     compaction kernel turns it into the next queue in vertex order, so that
+//     the next sweep reads its lists in address order (see k_compact_flags).
 //   xd: the distance v was last expanded with, so a vertex queued twice
 //     (near and far) is not expanded twice with the same distance.
 //   Th: long lists (more than kHeavyEntries entries) are expanded only when
@@ -259,8 +274,13 @@ __device__ __forceinline__ void warp_atomic_min(uint32_t* out, uint32_t x) {
 //     the wide window's few rounds.  Measured on GB300, Kronecker scale 24
 //     (hubs of 400 k entries) from host memory: re-expansion 2.49x -> 1.19x,
 //     84 -> 46 ms; no effect on graphs without long lists.
+//   kFlags: the next near frontier goes to `nflag` (compacted in vertex order)
+//     instead of the sweep's queue; for edge lists larger than the GPU's
+//     address translations cover (the compaction costs a scan of n bytes per
+//     sweep, 1.5 % of SSSP on a 6.4 GB graph that does not need it).
 constexpr uint32_t kHeavyEntries = 512;
-struct SsspOp {
+template <bool kFlags>
+struct SsspOpT {
     uint32_t* dist;
     uint32_t* qround;
     uint32_t* fflag;
@@ -272,10 +292,11 @@ struct SsspOp {
     uint32_t lmin;  // per-thread smallest distance sent to the far pile
     const uint64_t* off = nullptr;  // row offsets (for the list length of a vertex at or above Th)
     uint32_t Th = INF;
+    uint8_t* nflag = nullptr;       // next near frontier
     using S = uint32_t;
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = true;
-    static constexpr bool kPush = true;
+    static constexpr bool kPush = !kFlags;
     static constexpr int kSteps = 1;
     __device__ __forceinline__ S begin(uint32_t v) {
         const uint32_t d = __ldcg(dist + v);
@@ -304,27 +325,36 @@ struct SsspOp {
         if (nd >= cur) return false;  // cur may be stale, but only ever larger than the true value
         const uint32_t old = atomicMin(p, nd);
         if (nd >= old) return false;
-        if (nd < T) return atomicMax(qround + u, round + 1) < round + 1;
+        if (nd < T) {
+            const bool fresh = atomicMax(qround + u, round + 1) < round + 1;
+            if (!kFlags) return fresh;
+            if (fresh) nflag[u] = 1;
+            return false;
+        }
         lmin = nd < lmin ? nd : lmin;
         fflag[u] = 1u;  // idempotent: the split scans the flags, no queue to append to
         return false;
     }
     __device__ __forceinline__ void flush() { warp_atomic_min(far_min, lmin); }
 };
+using SsspOp = SsspOpT<false>;
+using SsspFlagsOp = SsspOpT<true>;
 
 // Multi-source BFS over up to 64 sources at once: bit b of a vertex's masks
 // belongs to source b.  One read of a list serves every source whose frontier
 // holds the vertex: the neighbour gains the frontier bits it has not been
 // visited by (visit is fixed during a sweep), collected with an atomic OR; the
-// first OR that lands on an empty mask queues the neighbour.
+// first OR that lands on an empty mask queues the neighbour (through the
+// next-frontier flags, compacted in vertex order).
 struct MsBfsOp {
     unsigned long long* front;
     const unsigned long long* seen;  // visit masks
     unsigned long long* next;
+    uint8_t* nflag;                  // newly reached vertices (compacted into the queue in vertex order)
     using S = unsigned long long;
     static constexpr S kSkip = 0ull;
     static constexpr bool kWeights = false;
-    static constexpr bool kPush = true;
+    static constexpr bool kPush = false;
     static constexpr int kSteps = 4;
     __device__ __forceinline__ S begin(uint32_t v) {
         const S f = front[v];
@@ -336,7 +366,8 @@ struct MsBfsOp {
         const S nb = f & ~seen[u];
         if (!nb) return false;
         if ((next[u] & nb) == nb) return false;  // a stale read only shows fewer bits
-        return atomicOr(next + u, nb) == 0ull;
+        if (atomicOr(next + u, nb) == 0ull) nflag[u] = 1;
+        return false;
     }
     static constexpr bool kPeek = false;
     __device__ __forceinline__ uint32_t peek(uint64_t) const { return 0; }
@@ -762,10 +793,13 @@ __global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op_in) {
 
 // Bottom-up BFS sweep (the pull direction of direction-optimising BFS, Beamer,
 // Asanovic and Patterson, SC 2012), for undirected graphs: every vertex not yet
-// reached reads its own list, G lanes per vertex in aligned 16-byte steps, and
-// stops at the first neighbour on level L; it then takes level L + 1 and joins
-// the next frontier.  When most vertices are already reached this reads a
-// small prefix of few lists instead of every list of a huge frontier.
+// reached looks for a neighbour on level L; it then takes level L + 1 and
+// joins the next frontier.  A lane first checks one vertex (coalesced level
+// reads) and its list heads in GPU memory, one at a time until a hit; only
+// the lists that this leaves undecided are read from the edge list, G lanes
+// per list in aligned 16-byte steps, stopping at the first hit.  When most
+// vertices are already reached, or most have a parent among their first
+// neighbours, this reads little of the edge list.
 // Only the owner writes level[v], and a vertex set to L + 1 during this sweep
 // never reads as L, so plain accesses suffice.
 template <int G, class Id = uint64_t>
@@ -778,55 +812,86 @@ __global__ void __launch_bounds__(256) k_bfs_bottom_up(Sweep c, uint32_t* level,
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t n = c.all_n;
     unsigned long long scanned = 0, lf = 0;
-    for (uint64_t base = warp * GPW; base < n; base += nwarps * GPW) {
-        const uint64_t v = base + grp;
-        uint64_t s = 0, e = 0, s0 = 0;
+    // one pass: 32 vertices per warp, one per lane
+    for (uint64_t base = warp * 32; base < n; base += nwarps * 32) {
+        const uint64_t v = base + lane;
+        uint64_t s = 0, e = 0;
+        bool found = false, pending = false;
         if (v < n && level[v] == INF) {
             s = c.off[v];
             e = c.off[v + 1];
+            if (c.heads) {
+                // the first kHeads neighbours are mirrored in GPU memory: check
+                // them there one by one (the first hit ends it), and leave the
+                // rest of the list, read from host memory, to the groups below
+                const uint4 h = *reinterpret_cast<const uint4*>(c.heads + v * kHeads);
+                const uint64_t k = e - s;
+                found = (k > 0 && level[h.x] == L) || (k > 1 && level[h.y] == L) || (k > 2 && level[h.z] == L) ||
+                        (k > 3 && level[h.w] == L);
+                pending = !found && k > (uint64_t)kHeads;
+                s += kHeads;
+            } else {
+                pending = e > s;
+            }
         }
-        s0 = s;
-        bool found = false;
-        if (c.heads) {
-            // the first kHeads neighbours are mirrored in GPU memory: check
-            // them there, and read the list from host memory only after them
-            bool hit = false;
-            if (glane < (uint32_t)kHeads && s + glane < e) hit = level[c.heads[v * kHeads + glane]] == L;
-            const unsigned hits = __ballot_sync(0xffffffffu, hit);
-            found = (hits & gmask) != 0;
-            s = s + kHeads < e ? s + kHeads : e;
+        if (found) {
+            level[v] = L + 1;
+            lf += e - (c.heads ? s - kHeads : s);
         }
-        const uint64_t a = aligned_start<Id>(s, c.shift);
-        const uint32_t steps = e > s ? (uint32_t)((e - a + E * G - 1) / (E * G)) : 0u;
-        for (uint32_t t = 0; __any_sync(0xffffffffu, t < steps && !found); t++) {
-            bool hit = false;
-            if (t < steps && !found) {
-                const uint64_t j = a + (uint64_t)t * (E * G) + E * glane;
-                if (j + E - 1 >= s && j < e) {
-                    uint32_t id[E];
-                    if (j + E - 1 < e) {
-                        ld_ids<Id>(c.cols, j, id);
-                    } else {
+        const unsigned fb = __ballot_sync(0xffffffffu, found);
+        if (fb) {  // append the warp's finds in vertex order, one atomic per warp
+            uint32_t pos = 0;
+            if (lane == 0) pos = atomicAdd(c.out_count, (uint32_t)__popc(fb));
+            pos = __shfl_sync(0xffffffffu, pos, 0);
+            if (found) c.out_q[pos + __popc(fb & ((1u << lane) - 1u))] = (uint32_t)v;
+        }
+        // lists still undecided: GPW of them at a time, G lanes each, read in
+        // aligned 16-byte steps until the first neighbour on level L
+        unsigned pend = __ballot_sync(0xffffffffu, pending);
+        while (pend) {
+            unsigned rest = pend;
+            for (uint32_t i = 0; i < grp && rest; i++) rest &= rest - 1u;  // this group's pending lane
+            const int src = rest ? __ffs((int)rest) - 1 : 0;
+            const bool mine = rest != 0;
+            for (uint32_t i = 0; i < (uint32_t)GPW && pend; i++) pend &= pend - 1u;
+            const uint64_t vv = __shfl_sync(0xffffffffu, v, src);
+            uint64_t ss = __shfl_sync(0xffffffffu, s, src);
+            uint64_t ee = __shfl_sync(0xffffffffu, e, src);
+            if (!mine) ss = ee = 0;
+            const uint64_t s0 = c.heads ? ss - kHeads : ss;
+            const uint64_t a = aligned_start<Id>(ss, c.shift);
+            const uint32_t steps = ee > ss ? (uint32_t)((ee - a + E * G - 1) / (E * G)) : 0u;
+            bool gfound = false;
+            for (uint32_t t = 0; __any_sync(0xffffffffu, t < steps && !gfound); t++) {
+                bool hit = false;
+                if (t < steps && !gfound) {
+                    const uint64_t j = a + (uint64_t)t * (E * G) + E * glane;
+                    if (j + E - 1 >= ss && j < ee) {
+                        uint32_t id[E];
+                        if (j + E - 1 < ee) {
+                            ld_ids<Id>(c.cols, j, id);
+                        } else {
 #pragma unroll
-                        for (int i = 0; i < E; i++) id[i] = (j + i < e) ? ld_id<Id>(c.cols, j + i) : 0u;
-                    }
+                            for (int x = 0; x < E; x++) id[x] = (j + x < ee) ? ld_id<Id>(c.cols, j + x) : 0u;
+                        }
 #pragma unroll
-                    for (int i = 0; i < E; i++) {
-                        if (j + i >= s && j + i < e) {
-                            hit = hit || level[id[i]] == L;
-                            scanned += 1;
+                        for (int x = 0; x < E; x++) {
+                            if (j + x >= ss && j + x < ee) {
+                                hit = hit || level[id[x]] == L;
+                                scanned += 1;
+                            }
                         }
                     }
                 }
+                // every lane must reach the ballot: evaluate it before combining
+                const unsigned hits = __ballot_sync(0xffffffffu, hit);
+                gfound = gfound || (hits & gmask) != 0;
             }
-            // every lane must reach the ballot: evaluate it before combining
-            const unsigned hits = __ballot_sync(0xffffffffu, hit);
-            found = found || (hits & gmask) != 0;
-        }
-        if (found && glane == 0) {
-            level[v] = L + 1;
-            lf += e - s0;
-            push(c.out_q, c.out_count, (uint32_t)v);
+            if (mine && gfound && glane == 0) {
+                level[vv] = L + 1;
+                lf += ee - s0;
+                push(c.out_q, c.out_count, (uint32_t)vv);
+            }
         }
     }
     add_scanned(c, scanned);
@@ -887,6 +952,70 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
     __syncwarp();
     add_scanned(c, scanned);
     op.flush();
+}
+
+// Frontier compaction: appends the vertices whose flag byte is set to q and
+// clears the flags.  Each thread takes 16 flags (one 16-byte load), and each
+// block turns a run of consecutive flags into one run of the queue, in vertex
+// order (one atomicAdd per block and pass), so the sweep that reads the queue
+// walks the edge list in address order within each block's range.  A sweep
+// whose queue came from pushes in arrival order reads its lists at random
+// across the whole edge list; once that list exceeds what the GPU's address
+// translations cover (tens of GB of host memory), those reads ran 8x slower
+// (measured on GB300, uniform 2^26 vertices with 25.8 GB of ids + weights:
+// 21 GB/s in arrival order against 160 GB/s in vertex order).  Flags are
+// bytes set with plain stores: a bitmap needs an atomic OR per vertex, and on
+// a dense BFS level (14 M new vertices into a 2 MB bitmap) those contended.
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
+    const uint32_t m = __vcmpne4(x, 0u);  // 0xff in every non-zero byte
+    return ((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u);
+}
+
+__device__ __forceinline__ void compact_flags_body(uint8_t* flags, uint64_t nchunks, uint32_t* q, uint32_t* count) {
+    __shared__ uint32_t warp_off[32];
+    __shared__ uint32_t block_base;
+    uint4* chunks = reinterpret_cast<uint4*>(flags);
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // every thread of a block runs the same number of passes (the bound is per block)
+    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < nchunks; base += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t ci = base + threadIdx.x;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (ci < nchunks) w = chunks[ci];
+        uint32_t mask = nonzero_bytes(w.x) | (nonzero_bytes(w.y) << 4) | (nonzero_bytes(w.z) << 8) |
+                        (nonzero_bytes(w.w) << 12);
+        if (mask) chunks[ci] = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t c = __popc(mask);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += t;
+        }
+        if (lane == 31) warp_off[wid] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (uint32_t i = 0; i < nw; i++) {
+                const uint32_t x = warp_off[i];
+                warp_off[i] = tot;
+                tot += x;
+            }
+            block_base = tot ? atomicAdd(count, tot) : 0u;
+        }
+        __syncthreads();
+        uint32_t pos = block_base + warp_off[wid] + incl - c;
+        while (mask) {
+            const uint32_t b = (uint32_t)__ffs((int)mask) - 1u;
+            mask &= mask - 1u;
+            q[pos++] = (uint32_t)(ci * 16u + b);
+        }
+        __syncthreads();  // warp_off and block_base are rewritten by the next pass
+    }
+}
+
+static __global__ void __launch_bounds__(256) k_compact_flags(uint8_t* flags, uint64_t nchunks, uint32_t* q,
+                                                              uint32_t* count) {
+    compact_flags_body(flags, nchunks, q, count);
 }
 
 // Block-aggregated queue append for kernels whose blocks step through the
@@ -1007,39 +1136,48 @@ struct SsspFixed {
     uint32_t* qround;
     uint32_t* fflag;
     uint32_t* xd;
+    uint8_t* nflag;       // next near frontier flags
+    uint64_t nchunks;     // 16-byte chunks of nflag
 };
 
-template <class Ctr>
+template <class Ctr, class OpT>
 __device__ __forceinline__ void sssp_loop_views(const SsspFixed& f, const SsspLoop& L, Ctr* ctr, Sweep* s,
-                                                SsspOp* op) {
+                                                OpT* op) {
     *s = f.base;
     s->in_q = f.q[L.side];
     s->in_count = &ctr->qcount[L.side];
     s->out_q = f.q[L.side ^ 1];
     s->out_count = &ctr->qcount[L.side ^ 1];
     s->large = &ctr->large[0];
-    *op = SsspOp{L.dist, f.qround, f.fflag, f.xd, &ctr->far_min, &ctr->overflow, L.T, L.sweeps, INF, f.base.off,
-                 L.Th};
+    *op = OpT{L.dist, f.qround, f.fflag, f.xd, &ctr->far_min, &ctr->overflow, L.T, L.sweeps, INF, f.base.off,
+                 L.Th, f.nflag};
 }
 
-template <class Ctr, int G, class Id>
+template <class Ctr, int G, class Id, bool kFlags>
 __global__ void __launch_bounds__(256) k_sssp_loop_sweep(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
     const SsspLoop L = *Lp;
     if (L.mode != 0) return;
     Sweep s;
-    SsspOp op;
+    SsspOpT<kFlags> op;
     sssp_loop_views(f, L, ctr, &s, &op);
-    expand_group_body<SsspOp, G, Id>(s, op);
+    expand_group_body<SsspOpT<kFlags>, G, Id>(s, op);
 }
 
-template <class Ctr, class Id>
+template <class Ctr, class Id, bool kFlags>
 __global__ void __launch_bounds__(256) k_sssp_loop_lists(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
     const SsspLoop L = *Lp;
     if (L.mode != 0) return;
     Sweep s;
-    SsspOp op;
+    SsspOpT<kFlags> op;
     sssp_loop_views(f, L, ctr, &s, &op);
-    expand_split_body<SsspOp, Id>(s, op);
+    expand_split_body<SsspOpT<kFlags>, Id>(s, op);
+}
+
+template <class Ctr>
+__global__ void __launch_bounds__(256) k_sssp_loop_compact(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
+    const SsspLoop L = *Lp;
+    if (L.mode != 0) return;
+    compact_flags_body(f.nflag, f.nchunks, f.q[L.side ^ 1], &ctr->qcount[L.side ^ 1]);
 }
 
 template <class Ctr>

@@ -161,7 +161,7 @@ emogi_status sweep_bottom_up_ids(Ctx& c, const Sweep& s, uint32_t* level, uint32
     const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
     if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
     const uint32_t G = std::min<uint32_t>(c.G, 8);
-    const int grid = grid_for(c, (uint64_t)c.g->n * G);
+    const int grid = grid_for(c, c.g->n);  // one vertex per lane, then G lanes per undecided list
     unsigned long long* fe = &ws.ctr->fedges;
     switch (G) {
         case 4: dev::k_bfs_bottom_up<4, Id><<<grid, kThreads, 0, c.st>>>(s, level, L, fe); break;
@@ -177,6 +177,30 @@ emogi_status sweep_bottom_up_ids(Ctx& c, const Sweep& s, uint32_t* level, uint32
 emogi_status sweep_bottom_up(Ctx& c, const Sweep& s, uint32_t* level, uint32_t L) {
     return c.g->id_bytes == 4 ? sweep_bottom_up_ids<uint32_t>(c, s, level, L)
                               : sweep_bottom_up_ids<uint64_t>(c, s, level, L);
+}
+
+// Turns the next-frontier flags into queue `side` (in vertex order) and
+// clears them.
+emogi_status compact_next(Ctx& c, int side) {
+    Workspace& ws = c.g->ws;
+    const uint64_t chunks = c.g->n / 16 + 1;
+    dev::k_compact_flags<<<grid_for(c, chunks), kThreads, 0, c.st>>>(ws.nflag, chunks, ws.q[side],
+                                                                     &ws.ctr->qcount[side]);
+    EMOGI_CUDA_TRY(cudaGetLastError());
+    c.kernel_launches++;
+    return EMOGI_OK;
+}
+
+// Clears what a call that ended early may have left set (far flags, the
+// next-frontier flags), and marks them in use until the call completes.
+emogi_status begin_flags(Ctx& c) {
+    Workspace& ws = c.g->ws;
+    if (ws.flags_dirty) {
+        EMOGI_CUDA_TRY(cudaMemsetAsync(ws.fflag, 0, c.g->n * 4, c.st));
+        EMOGI_CUDA_TRY(cudaMemsetAsync(ws.nflag, 0, (c.g->n / 16 + 1) * 16, c.st));
+    }
+    ws.flags_dirty = true;
+    return EMOGI_OK;
 }
 
 emogi_status read_counters(Ctx& c, bool after_sweep = true) {
@@ -291,16 +315,27 @@ emogi_status check_output(emogi_graph g, const Opts& o, void* out) {
     return EMOGI_OK;
 }
 
-template <class Id>
+template <class Id, bool kFlags>
 void record_sssp_sweeps(uint32_t G, int big, int lists, cudaStream_t cs, const dev::SsspFixed& f, dev::SsspLoop* L,
                         DevCounters* ctr) {
     switch (G) {
-        case 4: dev::k_sssp_loop_sweep<DevCounters, 4, Id><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
-        case 8: dev::k_sssp_loop_sweep<DevCounters, 8, Id><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
-        case 16: dev::k_sssp_loop_sweep<DevCounters, 16, Id><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
-        default: dev::k_sssp_loop_sweep<DevCounters, 32, Id><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
+        case 4: dev::k_sssp_loop_sweep<DevCounters, 4, Id, kFlags><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
+        case 8: dev::k_sssp_loop_sweep<DevCounters, 8, Id, kFlags><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
+        case 16: dev::k_sssp_loop_sweep<DevCounters, 16, Id, kFlags><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
+        default: dev::k_sssp_loop_sweep<DevCounters, 32, Id, kFlags><<<big, kThreads, 0, cs>>>(f, L, ctr); break;
     }
-    dev::k_sssp_loop_lists<DevCounters, Id><<<lists, kThreads, 0, cs>>>(f, L, ctr);
+    dev::k_sssp_loop_lists<DevCounters, Id, kFlags><<<lists, kThreads, 0, cs>>>(f, L, ctr);
+    if (kFlags) dev::k_sssp_loop_compact<DevCounters><<<big, kThreads, 0, cs>>>(f, L, ctr);
+}
+
+// Whether SSSP rebuilds its near frontiers in vertex order: for edge lists
+// (with weights) of 16 GiB or more, which a sweep in arrival order reads
+// scattered over more address range than the GPU's translations cover
+// (EMOGI_OPT_ORDERED_FRONTIER forces it).
+bool ordered_frontier(const Ctx& c) {
+    const emogi_graph g = c.g;
+    const uint64_t bytes = g->m * (g->id_bytes + (g->w ? 4u : 0u));
+    return (c.o.flags & EMOGI_OPT_ORDERED_FRONTIER) || bytes >= (16ull << 30);
 }
 
 // Records the device-driven SSSP loop of graph g as a CUDA graph (once per
@@ -309,7 +344,8 @@ void record_sssp_sweeps(uint32_t G, int big, int lists, cudaStream_t cs, const d
 emogi_status build_sssp_exec(Ctx& c) {
     emogi_graph g = c.g;
     Workspace& ws = g->ws;
-    if (ws.sssp_exec && ws.sssp_exec_G == c.G && ws.sssp_exec_chunk == c.chunk) return EMOGI_OK;
+    const uint32_t key = c.chunk * 2 + (ordered_frontier(c) ? 1u : 0u);
+    if (ws.sssp_exec && ws.sssp_exec_G == c.G && ws.sssp_exec_chunk == key) return EMOGI_OK;
     if (ws.sssp_exec) {
         cudaGraphExecDestroy(ws.sssp_exec);
         ws.sssp_exec = nullptr;
@@ -321,6 +357,8 @@ emogi_status build_sssp_exec(Ctx& c) {
     f.qround = ws.flag;
     f.fflag = ws.fflag;
     f.xd = ws.xd;
+    f.nflag = ws.nflag;
+    f.nchunks = g->n / 16 + 1;
     dev::SsspLoop* L = (dev::SsspLoop*)ws.sssp_loop;
     cudaGraph_t graph = nullptr;
     EMOGI_CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -342,8 +380,14 @@ emogi_status build_sssp_exec(Ctx& c) {
     e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const int big = c.sms * 8, lists = c.sms * 4;
-        if (g->id_bytes == 4) record_sssp_sweeps<uint32_t>(c.G, big, lists, cs, f, L, ws.ctr);
-        else record_sssp_sweeps<uint64_t>(c.G, big, lists, cs, f, L, ws.ctr);
+        const bool ord = ordered_frontier(c);
+        if (g->id_bytes == 4) {
+            if (ord) record_sssp_sweeps<uint32_t, true>(c.G, big, lists, cs, f, L, ws.ctr);
+            else record_sssp_sweeps<uint32_t, false>(c.G, big, lists, cs, f, L, ws.ctr);
+        } else {
+            if (ord) record_sssp_sweeps<uint64_t, true>(c.G, big, lists, cs, f, L, ws.ctr);
+            else record_sssp_sweeps<uint64_t, false>(c.G, big, lists, cs, f, L, ws.ctr);
+        }
         dev::k_sssp_loop_far<DevCounters><<<big, kThreads, 0, cs>>>(f, L, ws.ctr);
         dev::k_sssp_loop_control<DevCounters><<<1, 1, 0, cs>>>(L, ws.ctr, handle);
         cudaGraph_t captured = body;
@@ -356,7 +400,7 @@ emogi_status build_sssp_exec(Ctx& c) {
         return fail(EMOGI_E_CUDA, "recording the SSSP loop: %s", cudaGetErrorString(e));
     }
     ws.sssp_exec_G = c.G;
-    ws.sssp_exec_chunk = c.chunk;
+    ws.sssp_exec_chunk = key;
     return EMOGI_OK;
 }
 
@@ -382,6 +426,7 @@ emogi_status emogi_bfs(emogi_graph g, uint64_t src, uint32_t* level, const emogi
                                                                   nullptr, &ws.ctr->qcount[0]);
     EMOGI_CUDA_TRY(cudaGetLastError());
     c.kernel_launches++;
+    EMOGI_TRY(begin_flags(c));
     const bool diropt = (g->flags & EMOGI_LOAD_UNDIRECTED) && !(c.o.flags & EMOGI_OPT_TOP_DOWN_ONLY) &&
                         c.o.access == EMOGI_ACCESS_MERGED_ALIGNED;
     const bool beamer = c.o.flags & EMOGI_OPT_BEAMER;
@@ -406,8 +451,10 @@ emogi_status emogi_bfs(emogi_graph g, uint64_t src, uint32_t* level, const emogi
         EMOGI_CUDA_TRY(cudaMemsetAsync(&ws.ctr->fedges, 0, sizeof(unsigned long long), c.st));
         Sweep s = make_sweep(c, side, !top_down);
         if (top_down) {
-            dev::BfsOp op{state, it + 1, diropt ? g->d_off : nullptr, diropt ? &ws.ctr->fedges : nullptr};
+            dev::BfsBitsOp op{state, it + 1, diropt ? g->d_off : nullptr, diropt ? &ws.ctr->fedges : nullptr, 0,
+                              ws.nflag};
             EMOGI_TRY(sweep(c, s, op, nf));
+            EMOGI_TRY(compact_next(c, side ^ 1));
         } else {
             EMOGI_TRY(sweep_bottom_up(c, s, state, it));
         }
@@ -419,6 +466,7 @@ emogi_status emogi_bfs(emogi_graph g, uint64_t src, uint32_t* level, const emogi
         side ^= 1;
         it++;
     }
+    ws.flags_dirty = false;
     return finish(c, state, level, true, it, stats, false);
 }
 
@@ -434,7 +482,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
     DevCounters* ctr = ws.ctr;
     uint32_t* state = c.o.out_on_device ? dist : ws.state;
     const uint64_t n = g->n;
-    if (ws.flags_dirty) EMOGI_CUDA_TRY(cudaMemsetAsync(ws.fflag, 0, n * 4, c.st));
+    EMOGI_TRY(begin_flags(c));
     EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[0], c.st));
     EMOGI_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), c.st));
     EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->far_min, 0xFF, sizeof(uint32_t), c.st));
@@ -484,7 +532,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         it = hl->iters;
         sweeps = hl->sweeps;
         c.expand_launches += sweeps;
-        c.kernel_launches += 4ull * it;
+        c.kernel_launches += (ordered_frontier(c) ? 5ull : 4ull) * it;
     }
     uint64_t T = std::min<uint64_t>(delta, dev::INF);
     int side = 0;
@@ -496,6 +544,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
     // are rounds of almost no parallel work whose cost is latency; wider ones
     // there re-expand only the few vertices they hold.  (A threshold of n/64
     // measured worse on a uniform degree-32 graph: 1.64x re-expansion.)
+    const bool ordered = ordered_frontier(c);
     uint64_t widen = 1, window_work = 0;
     const uint64_t delta_heavy = std::max<uint64_t>(std::min<uint64_t>(delta, dev::INF) / 8, 1);
     uint32_t Th = dev::heavy_threshold(0, delta_heavy, T);
@@ -508,9 +557,16 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         if (nk > 0) {
             EMOGI_TRY(reset_sweep_counters(c, side));
             Sweep s = make_sweep(c, side, false);
-            dev::SsspOp op{state,    qround,   ws.fflag, ws.xd, &ctr->far_min, &ctr->overflow, (uint32_t)T, sweeps,
-                           dev::INF, g->d_off, Th};
-            EMOGI_TRY(sweep(c, s, op, nk));
+            if (ordered) {
+                dev::SsspFlagsOp op{state, qround, ws.fflag, ws.xd, &ctr->far_min, &ctr->overflow, (uint32_t)T,
+                                    sweeps, dev::INF, g->d_off, Th, ws.nflag};
+                EMOGI_TRY(sweep(c, s, op, nk));
+                EMOGI_TRY(compact_next(c, side ^ 1));
+            } else {
+                dev::SsspOp op{state, qround, ws.fflag, ws.xd, &ctr->far_min, &ctr->overflow, (uint32_t)T, sweeps,
+                               dev::INF, g->d_off, Th, nullptr};
+                EMOGI_TRY(sweep(c, s, op, nk));
+            }
             sweeps++;
             window_work += nk;
             EMOGI_TRY(read_counters(c));
@@ -599,6 +655,7 @@ emogi_status emogi_msbfs(emogi_graph g, const uint64_t* srcs, uint32_t k, uint32
     EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ms_front, 0, n * 8, c.st));
     EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ms_next, 0, n * 8, c.st));
     EMOGI_CUDA_TRY(cudaMemsetAsync(out, 0xFF, (size_t)k * n * 4, c.st));
+    EMOGI_TRY(begin_flags(c));
     dev::k_ms_init<<<1, 64, 0, c.st>>>(ms, ws.ms_visit, ws.ms_front, out, n, ws.q[0], &ws.ctr->qcount[0]);
     EMOGI_CUDA_TRY(cudaGetLastError());
     c.kernel_launches++;
@@ -610,7 +667,8 @@ emogi_status emogi_msbfs(emogi_graph g, const uint64_t* srcs, uint32_t k, uint32
         if (it > n + 1) return fail(EMOGI_E_TIMEOUT, "multi-source BFS did not converge in %u levels", it);
         EMOGI_TRY(reset_sweep_counters(c, side));
         Sweep s = make_sweep(c, side, false);
-        EMOGI_TRY(sweep(c, s, dev::MsBfsOp{ws.ms_front, ws.ms_visit, ws.ms_next}, kq));
+        EMOGI_TRY(sweep(c, s, dev::MsBfsOp{ws.ms_front, ws.ms_visit, ws.ms_next, ws.nflag}, kq));
+        EMOGI_TRY(compact_next(c, side ^ 1));
         dev::k_ms_finalize<<<grid_for(c, n), kThreads, 0, c.st>>>(ws.q[side ^ 1], &ws.ctr->qcount[side ^ 1],
                                                                    ws.ms_visit, ws.ms_front, ws.ms_next, out, n,
                                                                    it + 1);
@@ -621,6 +679,7 @@ emogi_status emogi_msbfs(emogi_graph g, const uint64_t* srcs, uint32_t k, uint32
         side ^= 1;
         it++;
     }
+    ws.flags_dirty = false;
     if (stats && n) {
         dev::k_ms_reached_edges<<<grid_for(c, n), kThreads, 0, c.st>>>(ws.ms_visit, g->d_off, (uint32_t)n,
                                                                          &ws.ctr->reached);

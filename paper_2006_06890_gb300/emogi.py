@@ -37,6 +37,7 @@ OPT_TOP_DOWN_ONLY = 2
 OPT_CC_FULL_PASS = 4
 OPT_HOST_LOOP = 8
 OPT_BEAMER = 16
+OPT_ORDERED_FRONTIER = 32
 
 
 class LibraryNotBuilt(RuntimeError):
@@ -260,7 +261,8 @@ def load_graph(g, placement="host", borrow=False, with_weights=True, heads=True,
 
 
 def _opts(access=None, granularity=0, chunk_lines=0, timeout_ns=0, stream=None, out_on_device=False,
-          time_kernels=False, delta=0, top_down_only=False, cc_full_pass=False, host_loop=False, beamer=False):
+          time_kernels=False, delta=0, top_down_only=False, cc_full_pass=False, host_loop=False, beamer=False,
+          ordered_frontier=False):
     o = Opts()
     o.struct_size = ctypes.sizeof(Opts)
     o.access = ACCESS[access] if isinstance(access, str) else int(access or 0)
@@ -272,7 +274,7 @@ def _opts(access=None, granularity=0, chunk_lines=0, timeout_ns=0, stream=None, 
     o.out_on_device = 1 if out_on_device else 0
     o.flags = (OPT_TIME_KERNELS if time_kernels else 0) | (OPT_TOP_DOWN_ONLY if top_down_only else 0) | \
         (OPT_CC_FULL_PASS if cc_full_pass else 0) | (OPT_HOST_LOOP if host_loop else 0) | \
-        (OPT_BEAMER if beamer else 0)
+        (OPT_BEAMER if beamer else 0) | (OPT_ORDERED_FRONTIER if ordered_frontier else 0)
     o.delta = int(delta)
     return o
 

@@ -218,6 +218,21 @@ def test_sssp_device_loop_equals_host_loop(name):
                 np.testing.assert_array_equal(E.sssp(h, s, granularity=G)[0], exp)
 
 
+@pytest.mark.parametrize("name", ["kron16", "urand14", "hub", "path", "directed", "residues"])
+def test_sssp_ordered_frontier(name):
+    """Near frontiers rebuilt in vertex order (flag per vertex + compaction;
+    automatic for edge lists of 16 GiB or more, forced here) give the oracle's
+    distances in both loops and at several window widths."""
+    g = graph(name)
+    with E.load_graph(g, placement="host") as h:
+        for s in sources(g):
+            exp = oracle.sssp_g(g, s)
+            np.testing.assert_array_equal(E.sssp(h, s, ordered_frontier=True)[0], exp)
+            np.testing.assert_array_equal(E.sssp(h, s, ordered_frontier=True, host_loop=True)[0], exp)
+            np.testing.assert_array_equal(E.sssp(h, s, ordered_frontier=True, delta=1, granularity=4)[0], exp)
+            np.testing.assert_array_equal(E.sssp(h, s)[0], exp)  # and back to the queue form
+
+
 def test_sssp_device_loop_time_bound():
     """The device loop checks %globaltimer at every iteration; a 1 ns bound
     stops it with EMOGI_E_TIMEOUT, and the next call is exact again."""
