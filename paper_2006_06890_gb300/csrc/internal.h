@@ -64,7 +64,9 @@ struct DevCounters {
     unsigned long long large[2];     // split-list work: (slots << 34) | items
     unsigned long long scanned;      // neighbour entries read
     unsigned long long reached;      // sum of out-degrees of reached vertices
-    unsigned long long fedges;       // BFS: sum of out-degrees of the next frontier
+    unsigned long long fedges;       // BFS / MS-BFS: sum of out-degrees of the next frontier
+    unsigned long long ms_pairs_edges; // MS-BFS: sum over new (source, vertex) pairs of the out-degree
+    unsigned long long ms_active;    // MS-BFS: sources whose frontier is non-empty
     uint32_t giant;                  // sampled CC: root of the largest sampled tree
     uint32_t pad2;
 };

@@ -1286,25 +1286,156 @@ static __global__ void k_compress(uint32_t* parent, uint32_t n) {
 
 // Multi-source BFS, end of a sweep: each newly reached vertex takes its new
 // bits into visit and into its frontier mask, and level L is written for each
-// new (source, vertex) pair; levels is k rows of n entries.
+// new (source, vertex) pair; levels is k rows of n entries.  For the choice
+// of the next level's direction it also sums the new frontier's out-degrees
+// (fedges), the out-degrees weighted by new sources (pairs_edges), and ORs
+// the sources whose frontier is non-empty (active).
+struct MsLevelStats {
+    unsigned long long* fedges;
+    unsigned long long* pairs_edges;
+    unsigned long long* active;
+};
+
 static __global__ void k_ms_finalize(const uint32_t* q, const uint32_t* count, unsigned long long* visit,
                                      unsigned long long* front, unsigned long long* next, uint32_t* levels,
-                                     uint64_t n, uint32_t level) {
+                                     uint64_t n, uint32_t level, const uint64_t* off, MsLevelStats st) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t k = *count;
-    for (uint64_t i = tid; i < k; i += nt) {
-        const uint32_t u = q[i];
-        unsigned long long nb = next[u];
-        next[u] = 0ull;
-        visit[u] |= nb;
-        front[u] = nb;
-        while (nb) {
-            const int b = __ffsll((long long)nb) - 1;
-            nb &= nb - 1;
-            levels[(uint64_t)b * n + u] = level;
+    unsigned long long fe = 0, pe = 0, act = 0;
+    for (uint64_t base = tid - (threadIdx.x & 31); base < k; base += nt) {
+        const uint64_t i = base + (threadIdx.x & 31);
+        if (i < k) {
+            const uint32_t u = q[i];
+            unsigned long long nb = next[u];
+            next[u] = 0ull;
+            visit[u] |= nb;
+            front[u] = nb;
+            const unsigned long long deg = off[u + 1] - off[u];
+            fe += deg;
+            pe += deg * (unsigned long long)__popcll(nb);
+            act |= nb;
+            while (nb) {
+                const int b = __ffsll((long long)nb) - 1;
+                nb &= nb - 1;
+                levels[(uint64_t)b * n + u] = level;
+            }
         }
     }
+    warp_atomic_add(st.fedges, fe);
+    warp_atomic_add(st.pairs_edges, pe);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) act |= __shfl_xor_sync(0xffffffffu, act, o);
+    if ((threadIdx.x & 31) == 0 && act) atomicOr(st.active, act);
+}
+
+// Multi-source BFS: clears the frontier masks of the level a bottom-up sweep
+// just finished with (a top-down sweep clears each one as it expands it).
+static __global__ void k_ms_clear_front(const uint32_t* q, const uint32_t* count, unsigned long long* front) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t k = *count;
+    for (uint64_t i = tid; i < k; i += nt) front[q[i]] = 0ull;
+}
+
+// Multi-source BFS, bottom-up level (the pull direction applied to all
+// sources at once, as Then et al., VLDB 2014, do for multi-source BFS over
+// bit sets): every vertex that some source with a non-empty frontier has not
+// reached (need = active & ~visit) ORs the frontier masks of its neighbours
+// into `got`, stopping once got == need.  A lane first takes one vertex and
+// its list heads in GPU memory; the lists this leaves undecided are read from
+// the edge list, G lanes per list, with the group's OR combined after every
+// step.  A vertex with new bits stores them in next (it is their only writer)
+// and flags itself for the ordered compaction.
+template <int G, class Id = uint64_t>
+__global__ void __launch_bounds__(256) k_ms_bottom_up(Sweep c, const unsigned long long* front,
+                                                      const unsigned long long* visit, unsigned long long* next,
+                                                      uint8_t* nflag, unsigned long long active) {
+    constexpr int GPW = 32 / G, E = IdWidth<Id>::kPerStep;
+    const uint32_t lane = threadIdx.x & 31u, glane = lane % G, grp = lane / G;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t n = c.all_n;
+    unsigned long long scanned = 0;
+    for (uint64_t base = warp * 32; base < n; base += nwarps * 32) {
+        const uint64_t v = base + lane;
+        uint64_t s = 0, e = 0;
+        unsigned long long need = 0, got = 0;
+        bool pending = false;
+        if (v < n) need = active & ~visit[v];
+        if (need) {
+            s = c.off[v];
+            e = c.off[v + 1];
+            if (c.heads) {
+                const uint4 h = *reinterpret_cast<const uint4*>(c.heads + v * kHeads);
+                const uint64_t k = e - s;
+                if (k > 0) got |= front[h.x] & need;
+                if (k > 1 && got != need) got |= front[h.y] & need;
+                if (k > 2 && got != need) got |= front[h.z] & need;
+                if (k > 3 && got != need) got |= front[h.w] & need;
+                pending = got != need && k > (uint64_t)kHeads;
+                s += kHeads;
+            } else {
+                pending = e > s;
+            }
+        }
+        if (!pending && got) {
+            next[v] = got;
+            nflag[v] = 1;
+        }
+        unsigned pend = __ballot_sync(0xffffffffu, pending);
+        while (pend) {
+            unsigned rest = pend;
+            for (uint32_t i = 0; i < grp && rest; i++) rest &= rest - 1u;  // this group's pending lane
+            const int src = rest ? __ffs((int)rest) - 1 : 0;
+            const bool mine = rest != 0;
+            for (uint32_t i = 0; i < (uint32_t)GPW && pend; i++) pend &= pend - 1u;
+            const uint64_t vv = __shfl_sync(0xffffffffu, v, src);
+            uint64_t ss = __shfl_sync(0xffffffffu, s, src);
+            uint64_t ee = __shfl_sync(0xffffffffu, e, src);
+            unsigned long long nd = __shfl_sync(0xffffffffu, need, src);
+            unsigned long long gg = __shfl_sync(0xffffffffu, got, src);
+            if (!mine) {
+                ss = ee = 0;
+                nd = 0ull;
+            }
+            const uint64_t a = aligned_start<Id>(ss, c.shift);
+            const uint32_t steps = ee > ss ? (uint32_t)((ee - a + E * G - 1) / (E * G)) : 0u;
+            bool done = !mine;
+            for (uint32_t t = 0; __any_sync(0xffffffffu, t < steps && !done); t++) {
+                unsigned long long part = 0;
+                if (t < steps && !done) {
+                    const uint64_t j = a + (uint64_t)t * (E * G) + E * glane;
+                    if (j + E - 1 >= ss && j < ee) {
+                        uint32_t id[E];
+                        if (j + E - 1 < ee) {
+                            ld_ids<Id>(c.cols, j, id);
+                        } else {
+#pragma unroll
+                            for (int x = 0; x < E; x++) id[x] = (j + x < ee) ? ld_id<Id>(c.cols, j + x) : 0u;
+                        }
+#pragma unroll
+                        for (int x = 0; x < E; x++) {
+                            if (j + x >= ss && j + x < ee) {
+                                part |= front[id[x]] & nd;
+                                scanned += 1;
+                            }
+                        }
+                    }
+                }
+                // every lane reaches the shuffles: the group's OR, then its test
+#pragma unroll
+                for (int o = G / 2; o > 0; o >>= 1) part |= __shfl_xor_sync(0xffffffffu, part, o);
+                gg |= part;
+                done = done || gg == nd;
+            }
+            if (mine && glane == 0 && gg) {
+                next[vv] = gg;
+                nflag[vv] = 1;
+            }
+        }
+    }
+    add_scanned(c, scanned);
 }
 
 struct MsSources {

@@ -203,6 +203,38 @@ emogi_status begin_flags(Ctx& c) {
     return EMOGI_OK;
 }
 
+// One bottom-up multi-source BFS level (k_ms_bottom_up).
+template <class Id>
+emogi_status ms_bottom_up_ids(Ctx& c, const Sweep& s, unsigned long long active) {
+    Workspace& ws = c.g->ws;
+    const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
+    if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
+    const int grid = grid_for(c, c.g->n);
+    if (std::min<uint32_t>(c.G, 8) == 4)
+        dev::k_ms_bottom_up<4, Id><<<grid, kThreads, 0, c.st>>>(s, ws.ms_front, ws.ms_visit, ws.ms_next, ws.nflag,
+                                                                 active);
+    else
+        dev::k_ms_bottom_up<8, Id><<<grid, kThreads, 0, c.st>>>(s, ws.ms_front, ws.ms_visit, ws.ms_next, ws.nflag,
+                                                                 active);
+    EMOGI_CUDA_TRY(cudaGetLastError());
+    if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[3], c.st));
+    c.kernel_launches++;
+    c.expand_launches++;
+    return EMOGI_OK;
+}
+
+// Multi-source BFS direction: bottom-up when the frontier's lists hold more
+// than 1/EMOGI_MS_ALPHA of the edges each source has left to explore on
+// average.  A pull for several sources stops only once every source it still
+// needs is found, so it pays later than a single-source pull (Beamer's 1/14).
+#ifndef EMOGI_MS_ALPHA
+#define EMOGI_MS_ALPHA 4
+#endif
+bool ms_bottom_up_pays(uint64_t mf, uint64_t m, uint32_t k, uint64_t pairs_edges) {
+    const double left = ((double)k * (double)m - (double)pairs_edges) / (double)k;
+    return (double)mf * EMOGI_MS_ALPHA > left;
+}
+
 emogi_status read_counters(Ctx& c, bool after_sweep = true) {
     Workspace& ws = c.g->ws;
     EMOGI_CUDA_TRY(cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c.st));
@@ -661,21 +693,41 @@ emogi_status emogi_msbfs(emogi_graph g, const uint64_t* srcs, uint32_t k, uint32
     c.kernel_launches++;
     EMOGI_TRY(read_counters(c, false));
     uint64_t kq = ws.h_ctr->qcount[0];
+    // direction-optimising as emogi_bfs (undirected graphs, aligned access)
+    const bool diropt = (g->flags & EMOGI_LOAD_UNDIRECTED) && !(c.o.flags & EMOGI_OPT_TOP_DOWN_ONLY) &&
+                        c.o.access == EMOGI_ACCESS_MERGED_ALIGNED;
+    unsigned long long active = k == 64 ? ~0ull : ((1ull << k) - 1ull);
+    uint64_t mf = 0;
+    const dev::MsLevelStats lst{&ws.ctr->fedges, &ws.ctr->ms_pairs_edges, &ws.ctr->ms_active};
     int side = 0;
     uint32_t it = 0;
     while (kq > 0) {
         if (it > n + 1) return fail(EMOGI_E_TIMEOUT, "multi-source BFS did not converge in %u levels", it);
         EMOGI_TRY(reset_sweep_counters(c, side));
         Sweep s = make_sweep(c, side, false);
-        EMOGI_TRY(sweep(c, s, dev::MsBfsOp{ws.ms_front, ws.ms_visit, ws.ms_next, ws.nflag}, kq));
+        const bool bottom_up = diropt && it > 0 && ms_bottom_up_pays(mf, g->m, k, ws.h_ctr->ms_pairs_edges);
+        if (bottom_up) {
+            if (g->id_bytes == 4) EMOGI_TRY(ms_bottom_up_ids<uint32_t>(c, make_sweep(c, side, true), active));
+            else EMOGI_TRY(ms_bottom_up_ids<uint64_t>(c, make_sweep(c, side, true), active));
+            dev::k_ms_clear_front<<<grid_for(c, kq), kThreads, 0, c.st>>>(ws.q[side], &ws.ctr->qcount[side],
+                                                                          ws.ms_front);
+            EMOGI_CUDA_TRY(cudaGetLastError());
+            c.kernel_launches++;
+        } else {
+            EMOGI_TRY(sweep(c, s, dev::MsBfsOp{ws.ms_front, ws.ms_visit, ws.ms_next, ws.nflag}, kq));
+        }
         EMOGI_TRY(compact_next(c, side ^ 1));
+        EMOGI_CUDA_TRY(cudaMemsetAsync(&ws.ctr->fedges, 0, sizeof(unsigned long long), c.st));
+        EMOGI_CUDA_TRY(cudaMemsetAsync(&ws.ctr->ms_active, 0, sizeof(unsigned long long), c.st));
         dev::k_ms_finalize<<<grid_for(c, n), kThreads, 0, c.st>>>(ws.q[side ^ 1], &ws.ctr->qcount[side ^ 1],
                                                                    ws.ms_visit, ws.ms_front, ws.ms_next, out, n,
-                                                                   it + 1);
+                                                                   it + 1, g->d_off, lst);
         EMOGI_CUDA_TRY(cudaGetLastError());
         c.kernel_launches++;
         EMOGI_TRY(read_counters(c));
         kq = ws.h_ctr->qcount[side ^ 1];
+        mf = ws.h_ctr->fedges;
+        active = ws.h_ctr->ms_active;
         side ^= 1;
         it++;
     }
