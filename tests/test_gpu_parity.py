@@ -402,6 +402,25 @@ def test_msbfs_graph_set(name, variant):
         np.testing.assert_array_equal(lv, oracle.msbfs(g.n, g.offsets, g.cols, srcs))
 
 
+@pytest.mark.parametrize("placement", ["device", "host"])
+@pytest.mark.parametrize("name", ["kron16", "urand14", "hub", "many"])
+def test_msbfs_directions(placement, name):
+    """Pulled (bottom-up) MS-BFS levels give the push-only levels, with or
+    without list heads, and read fewer entries on a Kronecker graph."""
+    g = many_components_graph() if name == "many" else graph(name)
+    srcs = ms_sources(g, 64 if g.n > 64 else 9)
+    exp = oracle.msbfs(g.n, g.offsets, g.cols, srcs)
+    for heads in (True, False):
+        with E.load_graph(g, placement=placement, heads=heads, with_weights=False) as h:
+            lv, st = E.msbfs(h, srcs)
+            np.testing.assert_array_equal(lv, exp, err_msg=f"heads={heads}")
+            lv2, st2 = E.msbfs(h, srcs, top_down_only=True)
+            np.testing.assert_array_equal(lv2, exp)
+            np.testing.assert_array_equal(E.msbfs(h, srcs, granularity=4)[0], exp)
+            if name == "kron16":
+                assert st["edges_scanned"] < st2["edges_scanned"]
+
+
 def test_msbfs_device_output_and_errors():
     g = graph("kron12")
     srcs = ms_sources(g, 9)
