@@ -742,6 +742,70 @@ __global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op_in) {
     expand_group_body<Op, G, Id>(c, op);
 }
 
+// Merged + aligned expansion over all vertices (CC's passes, the SSSP
+// overflow check), where begin() skips most vertices: a lane first takes one
+// vertex and calls begin() (32 vertices per warp and pass instead of 32/G),
+// then the vertices it keeps are read G lanes per list as above.
+template <class Op, int G, class Id = uint64_t>
+__global__ void __launch_bounds__(256) k_expand_all(Sweep c, Op op_in) {
+    Op op = op_in;
+    constexpr int GPW = 32 / G, E = IdWidth<Id>::kPerStep, LINE = IdWidth<Id>::kPerLine;
+    constexpr int KS = batch_steps<Op, Id>();
+    WarpQ wq = warpq_begin<Op>();
+    const uint32_t lane = threadIdx.x & 31u, glane = lane % G, grp = lane / G;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t n = c.all_n;
+    unsigned long long scanned = 0;
+    for (uint64_t base = warp * 32; base < n; base += nwarps * 32) {
+        const uint64_t v = base + lane;
+        typename Op::S st = Op::kSkip;
+        uint64_t s = 0, e = 0;
+        if (v < n) st = op.begin((uint32_t)v);
+        bool pending = false;
+        if (st != Op::kSkip) {
+            s = c.off[v];
+            e = c.off[v + 1];
+            scanned += e - s;
+            const uint64_t a = aligned_start<Id>(s, c.shift);
+            const uint64_t lines = e > s ? (e - a + LINE - 1) / LINE : 0;
+            if (lines > c.large_lines) defer(c, (uint32_t)v, (lines + c.chunk_lines - 1) / c.chunk_lines,
+                                             (unsigned long long)st);
+            else pending = e > s;
+        }
+        unsigned pend = __ballot_sync(0xffffffffu, pending);
+        while (pend) {
+            unsigned rest = pend;
+            for (uint32_t i = 0; i < grp && rest; i++) rest &= rest - 1u;  // this group's pending lane
+            const int src = rest ? __ffs((int)rest) - 1 : 0;
+            const bool mine = rest != 0;
+            for (uint32_t i = 0; i < (uint32_t)GPW && pend; i++) pend &= pend - 1u;
+            const uint32_t vv = (uint32_t)__shfl_sync(0xffffffffu, v, src);
+            const typename Op::S sv = __shfl_sync(0xffffffffu, st, src);
+            uint64_t ss = __shfl_sync(0xffffffffu, s, src);
+            uint64_t ee = __shfl_sync(0xffffffffu, e, src);
+            if (!mine) ss = ee = 0;
+            const uint64_t a = aligned_start<Id>(ss, c.shift);
+            const uint32_t steps = ee > ss ? (uint32_t)((ee - a + E * G - 1) / (E * G)) : 0u;
+            const uint32_t maxsteps = __reduce_max_sync(0xffffffffu, steps);
+            for (uint32_t t0 = 0; t0 < maxsteps; t0 += KS) {
+                typename StepOf<Id>::T p[KS];
+                typename CurOf<Id>::T cur[KS];
+#pragma unroll
+                for (int u = 0; u < KS; u++)
+                    p[u] = load_step<Op, Id>(c, a + (uint64_t)(t0 + u) * (E * G) + E * glane, ss, ee, t0 + u < steps);
+#pragma unroll
+                for (int u = 0; u < KS; u++) cur[u] = peek_step(op, p[u]);
+#pragma unroll
+                for (int u = 0; u < KS; u++) visit_step(c, op, sv, vv, p[u], cur[u], wq);
+            }
+        }
+    }
+    if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count);
+    add_scanned(c, scanned);
+    op.flush();
+}
+
 // Split lists: work item i of vertex lq_v[slot] covers lines
 // [i * chunk_lines, (i + 1) * chunk_lines) of its aligned list; one warp per
 // item, 16 bytes per lane (four 128-byte lines per step).

@@ -132,6 +132,18 @@ emogi_status sweep_ids(Ctx& c, const Sweep& s, const Op& op, uint64_t k) {
             c.kernel_launches += 1;
             break;
         default: {
+            if (!s.in_q) {  // every vertex: one lane per vertex first, G lanes per kept list
+                const int grid = grid_for(c, k);
+                switch (c.G) {
+                    case 4: dev::k_expand_all<Op, 4, Id><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                    case 8: dev::k_expand_all<Op, 8, Id><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                    case 16: dev::k_expand_all<Op, 16, Id><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                    default: dev::k_expand_all<Op, 32, Id><<<grid, kThreads, 0, c.st>>>(s, op); break;
+                }
+                dev::k_expand_split<Op, Id><<<c.sms * 4, kThreads, 0, c.st>>>(s, op);
+                c.kernel_launches += 2;
+                break;
+            }
             const int grid = grid_for(c, k * c.G);
             switch (c.G) {
                 case 4: dev::k_expand_group<Op, 4, Id><<<grid, kThreads, 0, c.st>>>(s, op); break;
