@@ -127,7 +127,7 @@ emogi_status ensure_workspace(emogi_graph g) {
         {(void**)&ws.q[0], n * 4, "frontier queue 0"},
         {(void**)&ws.q[1], n * 4, "frontier queue 1"},
         {(void**)&ws.state, n * 4, "vertex state"},
-        {(void**)&ws.flag, n * 4, "near flags"},
+        {(void**)&ws.qround, n * 4, "sweep stamps"},
         {(void**)&ws.fflag, n * 4, "far flags"},
         {(void**)&ws.xd, n * 4, "expanded distances"},
         {(void**)&ws.nflag, (n / 16 + 1) * 16, "next-frontier flags"},
@@ -145,7 +145,7 @@ emogi_status ensure_workspace(emogi_graph g) {
         ws.dev_bytes += it.bytes;
     }
     cudaError_t e = cudaHostAlloc((void**)&ws.h_ctr, sizeof(DevCounters), cudaHostAllocDefault);
-    if (e == cudaSuccess) e = cudaMemset(ws.flag, 0, n * 4);
+    if (e == cudaSuccess) e = cudaMemset(ws.qround, 0, n * 4);
     if (e == cudaSuccess) e = cudaMemset(ws.fflag, 0, n * 4);
     if (e == cudaSuccess) e = cudaMemset(ws.nflag, 0, (n / 16 + 1) * 16);
     for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&ws.ev[i]);
@@ -161,7 +161,7 @@ void release_workspace(emogi_graph g) {
     dev_free(ws.q[0], ws.n * 4);
     dev_free(ws.q[1], ws.n * 4);
     dev_free(ws.state, ws.n * 4);
-    dev_free(ws.flag, ws.n * 4);
+    dev_free(ws.qround, ws.n * 4);
     dev_free(ws.fflag, ws.n * 4);
     dev_free(ws.xd, ws.n * 4);
     dev_free(ws.nflag, (ws.n / 16 + 1) * 16);

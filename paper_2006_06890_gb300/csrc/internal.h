@@ -75,7 +75,7 @@ struct Workspace {
     uint64_t n = 0;
     uint32_t* q[2] = {nullptr, nullptr};   // frontier queues, n entries each
     uint32_t* state = nullptr;             // level / dist / parent when output is on the host
-    uint32_t* flag = nullptr;              // SSSP "in near frontier" flags, all zero between calls
+    uint32_t* qround = nullptr;            // SSSP sweep stamps: the sweep a vertex is queued for
     uint32_t* fflag = nullptr;             // SSSP "in the far pile" flags, all zero between calls
     uint32_t* xd = nullptr;                // SSSP distance of the last expansion
     uint8_t* nflag = nullptr;              // next frontier as one byte per vertex (n rounded up to 16), zero between calls

@@ -279,6 +279,9 @@ __device__ __forceinline__ void warp_atomic_min(uint32_t* out, uint32_t x) {
 //     address translations cover (the compaction costs a scan of n bytes per
 //     sweep, 1.5 % of SSSP on a 6.4 GB graph that does not need it).
 constexpr uint32_t kHeavyEntries = 512;
+#ifndef EMOGI_SSSP_MIN_BLOCKS
+#define EMOGI_SSSP_MIN_BLOCKS 1
+#endif
 template <bool kFlags>
 struct SsspOpT {
     uint32_t* dist;
@@ -297,6 +300,7 @@ struct SsspOpT {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = true;
     static constexpr bool kPush = !kFlags;
+    static constexpr int kMinBlocks = EMOGI_SSSP_MIN_BLOCKS;  // resident 256-thread blocks per SM asked of ptxas
     static constexpr int kSteps = 1;
     __device__ __forceinline__ S begin(uint32_t v) {
         const uint32_t d = __ldcg(dist + v);
@@ -683,6 +687,12 @@ constexpr int batch_steps() {
                                                                                : Op::kSteps;
 }
 
+// Resident blocks per SM a policy asks ptxas to fit (1 = no request).
+template <class Op, class = void> struct MinBlocks { static constexpr int value = 1; };
+template <class Op> struct MinBlocks<Op, decltype((void)Op::kMinBlocks)> {
+    static constexpr int value = Op::kMinBlocks;
+};
+
 // ------------------------------------------------------------------ kernels
 // Merged + aligned expansion with G lanes per vertex (G = 4, 8, 16, 32).
 // Loops are warp-uniform: a warp runs as many steps as its longest group.
@@ -737,7 +747,7 @@ __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
 }
 
 template <class Op, int G, class Id = uint64_t>
-__global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op_in) {
+__global__ void __launch_bounds__(256, MinBlocks<Op>::value) k_expand_group(Sweep c, Op op_in) {
     Op op = op_in;
     expand_group_body<Op, G, Id>(c, op);
 }
@@ -1172,16 +1182,14 @@ static __global__ void k_far_split(uint32_t n, uint32_t* fflag, const uint32_t* 
 // returns at once.  No host round trip separates iterations.
 struct SsspLoop {
     uint32_t side;        // near frontier parity
-    uint32_t fside;       // unused (kept for layout)
     uint32_t mode;        // 0 = sweep next, 1 = far split next, 2 = done
     uint32_t T;           // current threshold
     uint32_t sweeps;      // sweeps run (sweep stamp of the next sweep)
     uint32_t iters;       // sweeps + splits run
-    uint32_t delta;       // base window width
+    uint32_t delta;       // window width
     uint32_t error;       // 1 = the iteration cap was reached, 2 = the time bound
     unsigned long long cap;
     unsigned long long t0, timeout_ns;  // %globaltimer at the first iteration; bound on the loop
-    unsigned long long widen, window_work, light, heavy;
     uint32_t* dist;       // this call's distance array
     uint32_t Th;          // long lists wait while their distance is at or above this
     uint32_t delta_heavy; // width of the long lists' part of a window
@@ -1218,7 +1226,7 @@ __device__ __forceinline__ void sssp_loop_views(const SsspFixed& f, const SsspLo
 }
 
 template <class Ctr, int G, class Id, bool kFlags>
-__global__ void __launch_bounds__(256) k_sssp_loop_sweep(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
+__global__ void __launch_bounds__(256, EMOGI_SSSP_MIN_BLOCKS) k_sssp_loop_sweep(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
     const SsspLoop L = *Lp;
     if (L.mode != 0) return;
     Sweep s;
@@ -1264,7 +1272,6 @@ __global__ void k_sssp_loop_control(SsspLoop* Lp, Ctr* ctr, cudaGraphConditional
     // sent some (it then lowered far_min below INF)
     const bool far_pending = ctr->fcount[0] > 0 || ctr->far_min != INF;
     if (L.mode == 0) {
-        L.window_work += ctr->qcount[L.side];
         nk = ctr->qcount[L.side ^ 1];
         L.side ^= 1;
         L.sweeps++;
@@ -1288,10 +1295,7 @@ __global__ void k_sssp_loop_control(SsspLoop* Lp, Ctr* ctr, cudaGraphConditional
         ctr->large[0] = 0;
     } else if (fk > 0) {
         L.mode = 1;
-        if (L.light && L.window_work < L.light) L.widen = L.widen * 2 < 16 ? L.widen * 2 : 16;
-        else if (L.window_work > L.heavy) L.widen = L.widen / 2 > 1 ? L.widen / 2 : 1;
-        L.window_work = 0;
-        uint64_t Tn = (uint64_t)ctr->far_min + (uint64_t)L.delta * L.widen;
+        uint64_t Tn = (uint64_t)ctr->far_min + (uint64_t)L.delta;
         if (Tn <= L.T) Tn = (uint64_t)L.T + 1;
         L.T = Tn < (uint64_t)INF ? (uint32_t)Tn : INF;
         L.Th = heavy_threshold(ctr->far_min, L.delta_heavy, L.T);

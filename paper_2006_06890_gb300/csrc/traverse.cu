@@ -19,11 +19,6 @@ using dev::Sweep;
 
 constexpr int kThreads = 256;
 
-// SSSP windows that expanded fewer than n >> EMOGI_SSSP_LIGHT_SHIFT vertices
-// make the next window wider (0 = fixed windows).
-#ifndef EMOGI_SSSP_LIGHT_SHIFT
-#define EMOGI_SSSP_LIGHT_SHIFT 0
-#endif
 constexpr uint32_t kLargeLines = 32;  // lists above 32 lines (4 KiB) are split
 
 // EMOGI_TRACE=1 in the environment prints one line per sweep to stderr
@@ -49,14 +44,19 @@ struct Ctx {
     uint64_t kernel_launches = 0;
 };
 
-// Lanes per vertex when the caller leaves it open.  Measured on GB300 with a
-// uniform degree-32 graph: 8 lanes (128 bytes per step) beat 16 and 32 for
-// both placements because more lists are in flight per warp.
-uint32_t auto_granularity(double avg_degree) {
-    if (avg_degree >= 96.0) return 32;
-    if (avg_degree >= 48.0) return 16;
-    if (avg_degree >= 12.0) return 8;
-    return 4;
+// Lanes per vertex when the caller leaves it open: enough for a mean list in
+// about two 16-byte steps per lane.  Measured on GB300 with a uniform degree-32
+// graph: with uint64 ids 8 lanes (16 ids per step) beat 16 and 32 for both
+// placements, because more lists are in flight per warp, and beat 4 (SSSP
+// 43.3 against 44.5 ms); with uint32 ids 4 lanes (16 ids per step) beat 8
+// (SSSP 37.5 against 38.8 ms).
+uint32_t auto_granularity(double avg_degree, uint32_t id_bytes) {
+    uint32_t G = 4;
+    if (avg_degree >= 96.0) G = 32;
+    else if (avg_degree >= 48.0) G = 16;
+    else if (avg_degree >= 12.0) G = 8;
+    if (id_bytes == 4 && G > 4) G /= 2;  // a step carries twice the ids
+    return G;
 }
 
 // SSSP window width: a few times the weight of a vertex's cheapest out-edge
@@ -77,7 +77,7 @@ emogi_status setup(emogi_graph g, const emogi_opts* opts, Ctx* c) {
     EMOGI_CUDA_TRY(cudaSetDevice(g->device));
     EMOGI_TRY(ensure_workspace(g));
     c->st = c->o.stream ? c->o.stream : g->stream;
-    c->G = c->o.granularity ? c->o.granularity : auto_granularity(g->avg_degree);
+    c->G = c->o.granularity ? c->o.granularity : auto_granularity(g->avg_degree, g->id_bytes);
     c->chunk = c->o.chunk_lines ? c->o.chunk_lines : 32;
     c->sms = sm_count(g->device);
     if (trace_enabled()) c->o.flags |= EMOGI_OPT_TIME_KERNELS;
@@ -398,7 +398,7 @@ emogi_status build_sssp_exec(Ctx& c) {
     f.base = make_sweep(c, 0, false);
     f.q[0] = ws.q[0];
     f.q[1] = ws.q[1];
-    f.qround = ws.flag;
+    f.qround = ws.qround;
     f.fflag = ws.fflag;
     f.xd = ws.xd;
     f.nflag = ws.nflag;
@@ -531,7 +531,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
     EMOGI_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), c.st));
     EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->far_min, 0xFF, sizeof(uint32_t), c.st));
     EMOGI_CUDA_TRY(cudaMemsetAsync(ws.xd, 0xFF, n * 4, c.st));
-    uint32_t* qround = ws.flag;  // sweep stamps; all 0 = "queued for sweep 0" only matters for the source
+    uint32_t* qround = ws.qround;  // sweep stamps; all 0 = "queued for sweep 0" only matters for the source
     EMOGI_CUDA_TRY(cudaMemsetAsync(qround, 0, n * 4, c.st));
     dev::k_init_single<<<grid_for(c, n), kThreads, 0, c.st>>>(state, (uint32_t)n, (uint32_t)src, ws.q[0],
                                                                nullptr, &ctr->qcount[0]);
@@ -553,9 +553,6 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         hl->T = (uint32_t)std::min<uint64_t>(delta, dev::INF);
         hl->delta = (uint32_t)std::min<uint64_t>(delta, dev::INF);
         hl->cap = 4 * n + 8;
-        hl->widen = 1;
-        hl->light = EMOGI_SSSP_LIGHT_SHIFT ? std::max<uint64_t>(n >> EMOGI_SSSP_LIGHT_SHIFT, 256) : 0;
-        hl->heavy = std::max<uint64_t>(n >> 6, 1);
         hl->dist = state;
         hl->delta_heavy = (uint32_t)std::max<uint64_t>(std::min<uint64_t>(delta, dev::INF) / 8, 1);
         hl->Th = dev::heavy_threshold(0, hl->delta_heavy, hl->T);
@@ -581,19 +578,9 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
     uint64_t T = std::min<uint64_t>(delta, dev::INF);
     int side = 0;
     uint64_t nk = device_loop ? 0 : 1, fk = 0;
-    // Window widths adapt to the work they carry: a window whose sweeps
-    // expanded very few vertices (under n/65536: the first hops from the
-    // source, the long tail of far vertices) makes the next window twice as
-    // wide (up to 16x), a heavy one (over n/64) halves it again.  Tiny windows
-    // are rounds of almost no parallel work whose cost is latency; wider ones
-    // there re-expand only the few vertices they hold.  (A threshold of n/64
-    // measured worse on a uniform degree-32 graph: 1.64x re-expansion.)
     const bool ordered = ordered_frontier(c);
-    uint64_t widen = 1, window_work = 0;
     const uint64_t delta_heavy = std::max<uint64_t>(std::min<uint64_t>(delta, dev::INF) / 8, 1);
     uint32_t Th = dev::heavy_threshold(0, delta_heavy, T);
-    const uint64_t light = EMOGI_SSSP_LIGHT_SHIFT ? std::max<uint64_t>(n >> EMOGI_SSSP_LIGHT_SHIFT, 256) : 0;
-    const uint64_t heavy = std::max<uint64_t>(n >> 6, 1);
     while (nk > 0 || fk > 0) {
         // every sweep or split either expands a vertex with a smaller distance
         // than before or raises T; both are bounded
@@ -612,7 +599,6 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
                 EMOGI_TRY(sweep(c, s, op, nk));
             }
             sweeps++;
-            window_work += nk;
             EMOGI_TRY(read_counters(c));
             nk = ws.h_ctr->qcount[side ^ 1];
             fk = (ws.h_ctr->fcount[0] > 0 || ws.h_ctr->far_min != dev::INF) ? 1 : 0;
@@ -620,10 +606,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         } else {
             // near frontier empty: raise T past the smallest pending far distance
             const uint64_t fmin = ws.h_ctr->far_min;
-            if (window_work < light) widen = std::min<uint64_t>(widen * 2, 16);
-            else if (window_work > heavy) widen = std::max<uint64_t>(widen / 2, 1);
-            window_work = 0;
-            uint64_t Tn = fmin + delta * widen;
+            uint64_t Tn = fmin + delta;
             if (Tn <= T) Tn = T + 1;
             T = std::min<uint64_t>(Tn, dev::INF);
             Th = dev::heavy_threshold(fmin, delta_heavy, T);
