@@ -4,8 +4,8 @@ The compute path is the CUDA library ``libemogi.so`` (C ABI in
 ``include/emogi.h``); ``emogi`` is its thin ctypes binding.
 """
 from . import emogi  # noqa: F401
-from .emogi import (EmogiError, Graph, LibraryNotBuilt, bfs, cc, load_csr, load_graph,  # noqa: F401
-                    sssp)
+from .emogi import (Batch, EmogiError, Graph, LibraryNotBuilt, Server, bfs, bfs_batch, bfs_noalloc,  # noqa: F401
+                    cc, load_csr, load_csr32, load_graph, msbfs, sssp)
 
-__all__ = ["emogi", "EmogiError", "Graph", "LibraryNotBuilt", "bfs", "cc", "load_csr",
-           "load_graph", "sssp"]
+__all__ = ["emogi", "Batch", "EmogiError", "Graph", "LibraryNotBuilt", "Server", "bfs", "bfs_batch",
+           "bfs_noalloc", "cc", "load_csr", "load_csr32", "load_graph", "msbfs", "sssp"]

@@ -279,9 +279,6 @@ __device__ __forceinline__ void warp_atomic_min(uint32_t* out, uint32_t x) {
 //     address translations cover (the compaction costs a scan of n bytes per
 //     sweep, 1.5 % of SSSP on a 6.4 GB graph that does not need it).
 constexpr uint32_t kHeavyEntries = 512;
-#ifndef EMOGI_SSSP_MIN_BLOCKS
-#define EMOGI_SSSP_MIN_BLOCKS 1
-#endif
 template <bool kFlags>
 struct SsspOpT {
     uint32_t* dist;
@@ -300,7 +297,6 @@ struct SsspOpT {
     static constexpr S kSkip = INF;
     static constexpr bool kWeights = true;
     static constexpr bool kPush = !kFlags;
-    static constexpr int kMinBlocks = EMOGI_SSSP_MIN_BLOCKS;  // resident 256-thread blocks per SM asked of ptxas
     static constexpr int kSteps = 1;
     __device__ __forceinline__ S begin(uint32_t v) {
         const uint32_t d = __ldcg(dist + v);
@@ -687,12 +683,6 @@ constexpr int batch_steps() {
                                                                                : Op::kSteps;
 }
 
-// Resident blocks per SM a policy asks ptxas to fit (1 = no request).
-template <class Op, class = void> struct MinBlocks { static constexpr int value = 1; };
-template <class Op> struct MinBlocks<Op, decltype((void)Op::kMinBlocks)> {
-    static constexpr int value = Op::kMinBlocks;
-};
-
 // ------------------------------------------------------------------ kernels
 // Merged + aligned expansion with G lanes per vertex (G = 4, 8, 16, 32).
 // Loops are warp-uniform: a warp runs as many steps as its longest group.
@@ -747,7 +737,7 @@ __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
 }
 
 template <class Op, int G, class Id = uint64_t>
-__global__ void __launch_bounds__(256, MinBlocks<Op>::value) k_expand_group(Sweep c, Op op_in) {
+__global__ void __launch_bounds__(256) k_expand_group(Sweep c, Op op_in) {
     Op op = op_in;
     expand_group_body<Op, G, Id>(c, op);
 }
@@ -1226,7 +1216,7 @@ __device__ __forceinline__ void sssp_loop_views(const SsspFixed& f, const SsspLo
 }
 
 template <class Ctr, int G, class Id, bool kFlags>
-__global__ void __launch_bounds__(256, EMOGI_SSSP_MIN_BLOCKS) k_sssp_loop_sweep(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
+__global__ void __launch_bounds__(256) k_sssp_loop_sweep(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
     const SsspLoop L = *Lp;
     if (L.mode != 0) return;
     Sweep s;
