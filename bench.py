@@ -220,6 +220,21 @@ def step_link_bytes(stats):
             LINK_BYTES_PER_ALG_BYTE["cc"] * 8 * sc["edges_scanned"])
 
 
+def combine_over_ranks(ms, units, world, device="cuda"):
+    """Across replicas: the timed region lasts as long as the slowest rank's,
+    and the work is every rank's (each rank runs its own copy of the step on
+    its own GPU; there is no data-path collective)."""
+    if world <= 1:
+        return ms, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def time_loop(torch, E, h, srcs, stream, steps, warmup, outs):
     for i in range(warmup):
         run_step(E, h, srcs[i % len(srcs)], stream, outs)
@@ -270,13 +285,8 @@ def ours(args):
     with ClockSampler(local) as clk:
         ms, wall, per = time_loop(torch, E, h, srcs, stream, args.steps, args.warmup, outs)
     barrier()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    teps_edges = sum(step_teps_edges(p) for p in per)
-    value = teps_edges * world / (ms * 1e-3) / 1e9
+    ms, teps_edges = combine_over_ranks(ms, sum(step_teps_edges(p) for p in per), world)
+    value = teps_edges / (ms * 1e-3) / 1e9
     expand_ms = sum(s["expand_ms"] for p in per for s in p)
     alg_bytes = sum(step_alg_bytes(p) for p in per)
     launches = sum(s["kernel_launches"] for p in per for s in p)
@@ -297,9 +307,13 @@ def ours(args):
     barrier()
     ms_e2e, wall_e2e, per_e2e = time_loop(torch, E, h, srcs, stream, e2e_steps, 1, host_outs)
     barrier()
-    e2e_value = sum(step_teps_edges(p) for p in per_e2e) * world / (ms_e2e * 1e-3) / 1e9
+    ms_e2e, e2e_edges = combine_over_ranks(ms_e2e, sum(step_teps_edges(p) for p in per_e2e), world)
+    e2e_value = e2e_edges / (ms_e2e * 1e-3) / 1e9
+    barrier()
     ms_pg, _, per_pg = time_loop(torch, E, h, srcs, stream, e2e_steps, 1, None)
-    e2e_pageable = sum(step_teps_edges(p) for p in per_pg) * world / (ms_pg * 1e-3) / 1e9
+    barrier()
+    ms_pg, pg_edges = combine_over_ranks(ms_pg, sum(step_teps_edges(p) for p in per_pg), world)
+    e2e_pageable = pg_edges / (ms_pg * 1e-3) / 1e9
     del host_outs
 
     result = {
