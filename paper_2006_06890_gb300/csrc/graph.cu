@@ -445,6 +445,7 @@ static emogi_status load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets
     g->flags = flags;
     g->place = place;
     g->avg_degree = n ? (double)m / (double)n : 0.0;
+    for (uint64_t v = 0; v < n; v++) g->max_degree = std::max<uint64_t>(g->max_degree, row_offsets[v + 1] - row_offsets[v]);
     auto bail = [&](emogi_status s) {
         emogi_free_graph(g);
         return s;
@@ -575,6 +576,7 @@ emogi_status emogi_graph_share(emogi_graph g, emogi_graph* out) {
     h->w = g->w;
     h->shift = g->shift;
     h->avg_degree = g->avg_degree;
+    h->max_degree = g->max_degree;
     h->avg_weight = g->avg_weight;
     h->shared = true;
     cudaError_t e = cudaSetDevice(h->device);

@@ -123,6 +123,7 @@ struct emogi_graph_s {
     cudaStream_t stream = nullptr;
     emogi::Workspace ws;
     double avg_degree = 0.0;
+    uint64_t max_degree = 0;
     double avg_weight = 0.0;           // mean of a sample of the weights
     bool shared = false;               // a view made by emogi_graph_share: the arrays belong to another handle
 };

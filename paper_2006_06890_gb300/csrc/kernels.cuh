@@ -1183,6 +1183,7 @@ struct SsspLoop {
     uint32_t* dist;       // this call's distance array
     uint32_t Th;          // long lists wait while their distance is at or above this
     uint32_t delta_heavy; // width of the long lists' part of a window
+    unsigned long long tail;  // a sweep leaving fewer near vertices than this splits the far pile at once
 };
 
 // The long lists' threshold of a window that starts at `lo`.
@@ -1261,6 +1262,7 @@ __global__ void k_sssp_loop_control(SsspLoop* Lp, Ctr* ctr, cudaGraphConditional
     // far vertices are pending if the last split kept some or a sweep since
     // sent some (it then lowered far_min below INF)
     const bool far_pending = ctr->fcount[0] > 0 || ctr->far_min != INF;
+    const bool after_sweep = L.mode == 0;
     if (L.mode == 0) {
         nk = ctr->qcount[L.side ^ 1];
         L.side ^= 1;
@@ -1279,17 +1281,19 @@ __global__ void k_sssp_loop_control(SsspLoop* Lp, Ctr* ctr, cudaGraphConditional
     } else if (now - L.t0 > L.timeout_ns) {
         L.error = 2;
         L.mode = 2;
-    } else if (nk > 0) {
+    } else if (nk > 0 && !(after_sweep && fk > 0 && nk < L.tail)) {
         L.mode = 0;
         ctr->qcount[L.side ^ 1] = 0;
         ctr->large[0] = 0;
     } else if (fk > 0) {
+        // near frontier empty, or down to the window's tail (which stays in
+        // the queue; the split appends behind it)
         L.mode = 1;
         uint64_t Tn = (uint64_t)ctr->far_min + (uint64_t)L.delta;
         if (Tn <= L.T) Tn = (uint64_t)L.T + 1;
         L.T = Tn < (uint64_t)INF ? (uint32_t)Tn : INF;
         L.Th = heavy_threshold(ctr->far_min, L.delta_heavy, L.T);
-        ctr->qcount[L.side] = 0;
+        if (nk == 0) ctr->qcount[L.side] = 0;
         ctr->fcount[0] = 0;
         ctr->far_min = INF;
     } else {

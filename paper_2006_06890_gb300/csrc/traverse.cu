@@ -64,6 +64,21 @@ uint32_t auto_granularity(double avg_degree, uint32_t id_bytes) {
 // shortest-path tree.  Measured on GB300 with weights in [1, 255] and degree
 // 32: width 16 re-expands 3% of the edges in 100 rounds, width 8 0.7% in 155
 // rounds, plain Bellman-Ford 360% in 35 rounds.
+// A window's tail: once a sweep leaves fewer near vertices than this, the far
+// pile is split at once and the tail joins the next window's first sweep
+// instead of draining in a run of small, latency-bound sweeps (0 = off).
+// Measured on GB300, uniform 2^24 degree 32: SSSP 43.6 -> 42.7 ms from host
+// memory, 12.6 -> 11.7 ms from HBM, the same re-expansion.  On graphs with
+// long lists (Kronecker scale 24) it let hubs be improved after their window
+// moved on and doubled the re-expansion (46 -> 77 ms), so it is off there.
+#ifndef EMOGI_SSSP_TAIL_SHIFT
+#define EMOGI_SSSP_TAIL_SHIFT 12
+#endif
+uint64_t sssp_tail(emogi_graph g) {
+    if (!EMOGI_SSSP_TAIL_SHIFT || g->max_degree > dev::kHeavyEntries) return 0;
+    return std::max<uint64_t>(g->n >> EMOGI_SSSP_TAIL_SHIFT, 256);
+}
+
 uint64_t auto_delta(emogi_graph g) {
     const double d = g->avg_degree > 1.0 ? g->avg_degree : 1.0;
     const double x = g->avg_weight * 4.0 / d;
@@ -556,6 +571,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         hl->dist = state;
         hl->delta_heavy = (uint32_t)std::max<uint64_t>(std::min<uint64_t>(delta, dev::INF) / 8, 1);
         hl->Th = dev::heavy_threshold(0, hl->delta_heavy, hl->T);
+        hl->tail = sssp_tail(g);
         // the loop runs on the device: bound it in time as well (the caller's
         // timeout_ns when given, else one minute)
         hl->timeout_ns = (opts && opts->timeout_ns) ? opts->timeout_ns : 60000000000ull;
@@ -579,13 +595,15 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
     int side = 0;
     uint64_t nk = device_loop ? 0 : 1, fk = 0;
     const bool ordered = ordered_frontier(c);
+    const uint64_t tail = sssp_tail(g);
     const uint64_t delta_heavy = std::max<uint64_t>(std::min<uint64_t>(delta, dev::INF) / 8, 1);
     uint32_t Th = dev::heavy_threshold(0, delta_heavy, T);
+    bool merge_tail = false;
     while (nk > 0 || fk > 0) {
         // every sweep or split either expands a vertex with a smaller distance
         // than before or raises T; both are bounded
         if (it > 4 * n + 8) return fail(EMOGI_E_TIMEOUT, "SSSP did not converge in %u rounds", it);
-        if (nk > 0) {
+        if (nk > 0 && !merge_tail) {
             EMOGI_TRY(reset_sweep_counters(c, side));
             Sweep s = make_sweep(c, side, false);
             if (ordered) {
@@ -603,14 +621,18 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
             nk = ws.h_ctr->qcount[side ^ 1];
             fk = (ws.h_ctr->fcount[0] > 0 || ws.h_ctr->far_min != dev::INF) ? 1 : 0;
             side ^= 1;
+            merge_tail = nk > 0 && nk < tail && fk > 0;
         } else {
-            // near frontier empty: raise T past the smallest pending far distance
+            // near frontier empty, or down to the window's tail: raise T past
+            // the smallest pending far distance; a tail stays in the queue and
+            // the split appends behind it
             const uint64_t fmin = ws.h_ctr->far_min;
             uint64_t Tn = fmin + delta;
             if (Tn <= T) Tn = T + 1;
             T = std::min<uint64_t>(Tn, dev::INF);
             Th = dev::heavy_threshold(fmin, delta_heavy, T);
-            EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->qcount[side], 0, sizeof(uint32_t), c.st));
+            if (!merge_tail) EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->qcount[side], 0, sizeof(uint32_t), c.st));
+            merge_tail = false;
             EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->fcount[0], 0, sizeof(uint32_t), c.st));
             EMOGI_CUDA_TRY(cudaMemsetAsync(&ctr->far_min, 0xFF, sizeof(uint32_t), c.st));
             dev::k_far_split<<<grid_for(c, n), kThreads, 0, c.st>>>((uint32_t)n, ws.fflag, state, ws.xd, qround,
