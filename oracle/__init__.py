@@ -1,4 +1,4 @@
-"""CPU oracle for BFS / SSSP / CC / multi-source BFS: TEST INFRASTRUCTURE ONLY.
+"""CPU oracle for BFS / SSSP / CC / multi-source BFS / PageRank: TEST INFRASTRUCTURE ONLY.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
 and reference legs may import this package.  The CUDA library never calls it
@@ -50,7 +50,8 @@ def _lib():
         lib.oracle_bfs.argtypes = [u64, p, p, u64, p]
         lib.oracle_sssp.argtypes = [u64, p, p, p, u64, p]
         lib.oracle_cc.argtypes = [u64, p, p, p]
-        for f in (lib.oracle_bfs, lib.oracle_sssp, lib.oracle_cc):
+        lib.oracle_pagerank.argtypes = [u64, p, p, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, p, p]
+        for f in (lib.oracle_bfs, lib.oracle_sssp, lib.oracle_cc, lib.oracle_pagerank):
             f.restype = ctypes.c_int
         _lib_handle = lib
     return _lib_handle
@@ -104,6 +105,23 @@ def msbfs(n, offsets, cols, sources) -> np.ndarray:
     for k, s in enumerate(srcs):
         out[k] = bfs(n, offsets, cols, s)
     return out
+
+
+def pagerank(n, offsets, cols, damping=0.85, tol=1e-10, max_iter=100):
+    """(ranks float64[n], iterations) by power iteration (oracle.c)."""
+    off, poff = _arr(offsets, np.uint64)
+    col, pcol = _arr(cols, np.uint64)
+    out = np.empty(max(n, 1), dtype=np.float64)
+    it = np.zeros(1, dtype=np.uint32)
+    rc = _lib().oracle_pagerank(n, poff, pcol, float(damping), float(tol), int(max_iter),
+                                ctypes.c_void_p(out.ctypes.data), ctypes.c_void_p(it.ctypes.data))
+    if rc != 0:
+        raise OracleError(f"oracle_pagerank failed ({rc})")
+    return out[:n], int(it[0])
+
+
+def pagerank_g(g, damping=0.85, tol=1e-10, max_iter=100):
+    return pagerank(g.n, g.offsets, g.cols, damping, tol, max_iter)
 
 
 def bfs_g(g, src):

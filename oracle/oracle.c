@@ -20,6 +20,15 @@
  *                 the smaller), connected components of an undirected graph
  *                 (Sec. 5.4).  label[v] = the smallest vertex id in v's
  *                 component.
+ *   oracle_pagerank - PageRank by power iteration in double precision (the
+ *                 fourth application of Sec. 5.4), every vertex active each
+ *                 iteration.  This is an iteration, not a closed form, so it
+ *                 follows the steps in order: start from 1/n; each iteration
+ *                 gives every vertex (1 - d)/n, plus d times the rank of the
+ *                 vertices without out-edges divided by n, plus d times
+ *                 rank(v)/outdeg(v) for each edge v -> u it receives; stop
+ *                 after max_iter iterations or once the L1 change is below
+ *                 tol.  Parallel edges and self-loops count as edges.
  *
  * Build: gcc -O2 -shared -fPIC oracle.c -o _oracle.so
  */
@@ -147,5 +156,38 @@ int oracle_cc(uint64_t n, const uint64_t* offsets, const uint64_t* cols, uint32_
     }
     for (uint64_t v = 0; v < n; v++) label[v] = (uint32_t)uf_find(parent, v);
     free(parent);
+    return 0;
+}
+
+/* PageRank, power iteration (see the header).  rank: n doubles, output.
+ * Returns the iterations run through *iters; 0 on success, 2 on allocation
+ * failure. */
+int oracle_pagerank(uint64_t n, const uint64_t* offsets, const uint64_t* cols, double damping, double tol,
+                    uint32_t max_iter, double* rank, uint32_t* iters) {
+    *iters = 0;
+    if (n == 0) return 0;
+    double* next = (double*)malloc(n * sizeof(double));
+    if (!next) return 2;
+    for (uint64_t v = 0; v < n; v++) rank[v] = 1.0 / (double)n;
+    for (uint32_t it = 0; it < max_iter; it++) {
+        double dangling = 0.0;
+        for (uint64_t v = 0; v < n; v++)
+            if (offsets[v + 1] == offsets[v]) dangling += rank[v];
+        const double base = (1.0 - damping) / (double)n + damping * dangling / (double)n;
+        for (uint64_t u = 0; u < n; u++) next[u] = base;
+        for (uint64_t v = 0; v < n; v++) {
+            const uint64_t deg = offsets[v + 1] - offsets[v];
+            for (uint64_t i = offsets[v]; i < offsets[v + 1]; i++)
+                next[cols[i]] += damping * rank[v] / (double)deg;
+        }
+        double change = 0.0;
+        for (uint64_t v = 0; v < n; v++) {
+            change += next[v] > rank[v] ? next[v] - rank[v] : rank[v] - next[v];
+            rank[v] = next[v];
+        }
+        *iters = it + 1;
+        if (change < tol) break;
+    }
+    free(next);
     return 0;
 }

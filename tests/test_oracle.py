@@ -82,6 +82,7 @@ class Impl:
         lib.oracle_bfs.argtypes = [u64, p, p, u64, p]
         lib.oracle_sssp.argtypes = [u64, p, p, p, u64, p]
         lib.oracle_cc.argtypes = [u64, p, p, p]
+        lib.oracle_pagerank.argtypes = [u64, p, p, ctypes.c_double, ctypes.c_double, ctypes.c_uint32, p, p]
         self.lib = lib
 
     @staticmethod
@@ -109,6 +110,16 @@ class Impl:
         col = np.ascontiguousarray(g.cols, dtype=np.uint64)
         assert self.lib.oracle_cc(g.n, self._p(off), self._p(col), self._p(out)) == 0
         return out[:g.n]
+
+
+    def pagerank(self, g, damping=0.85, tol=1e-15, max_iter=2000):
+        out = np.empty(max(g.n, 1), dtype=np.float64)
+        it = np.zeros(1, dtype=np.uint32)
+        off = np.ascontiguousarray(g.offsets, dtype=np.uint64)
+        col = np.ascontiguousarray(g.cols, dtype=np.uint64)
+        assert self.lib.oracle_pagerank(g.n, self._p(off), self._p(col), damping, tol, max_iter, self._p(out),
+                                        self._p(it)) == 0
+        return out[:g.n], int(it[0])
 
 
 @pytest.fixture(scope="module")
@@ -374,6 +385,67 @@ def test_uniform_graph_alignment_statistic():
 
 
 # ---------------------------------------------------------------- mutations
+# ------------------------------------------------------------------ PageRank pins
+def pagerank_exact(g, d):
+    """The fixed point of the PageRank iteration, by a dense linear solve:
+    r = (1-d)/n + d (P^T r + (dangling . r)/n), P[v,u] = edges v->u / outdeg v."""
+    n = g.n
+    P = np.zeros((n, n))
+    dang = np.zeros(n)
+    deg = np.diff(g.offsets).astype(np.int64)
+    for v in range(n):
+        if deg[v] == 0:
+            dang[v] = 1.0
+        for i in range(int(g.offsets[v]), int(g.offsets[v + 1])):
+            P[v, int(g.cols[i])] += 1.0 / deg[v]
+    A = np.eye(n) - d * P.T - (d / n) * np.outer(np.ones(n), dang)
+    return np.linalg.solve(A, np.full(n, (1.0 - d) / n))
+
+
+def check_pagerank(impl):
+    # exact fixed point on small directed multigraphs (dangling vertices,
+    # parallel edges, self-loops) and undirected graphs, two damping factors
+    small = list(random_directed_multigraphs(40, 12)) + list(all_undirected_graphs(4))[::7]
+    for g in small:
+        for d in (0.85, 0.5):
+            r, it = impl.pagerank(g, d)
+            assert it < 2000
+            assert np.allclose(r, pagerank_exact(g, d), rtol=0, atol=1e-12)
+    # closed forms: a star's centre, a cycle and a complete graph (uniform)
+    d, n = 0.85, 25
+    r, _ = impl.pagerank(gg.star_graph(n), d)
+    assert abs(r[0] - (1 + d * (n - 1)) / (n * (1 + d))) < 1e-12
+    assert np.allclose(r[1:], ((1 - d) / n + d * r[0] / (n - 1)), atol=1e-12)
+    ring = gg.csr_from_edges(n, np.arange(n), (np.arange(n) + 1) % n, symmetrize=True)
+    assert np.allclose(impl.pagerank(ring, d)[0], 1.0 / n, atol=1e-14)
+    assert np.allclose(impl.pagerank(gg.complete_graph(9), d)[0], 1.0 / 9, atol=1e-14)
+    # invariants on a larger graph: a probability vector, and a fixed point
+    g = gg.kronecker(10, 8, seed=4)
+    r, it = impl.pagerank(g, d, tol=1e-13)
+    assert abs(r.sum() - 1.0) < 1e-12 and np.all(r > 0)
+    r2, _ = impl.pagerank(g, d, tol=0.0, max_iter=it + 1)
+    assert np.abs(r2 - r).sum() < 1e-12
+
+
+def test_pagerank_pins(impl):
+    check_pagerank(impl)
+
+
+def test_pagerank_against_networkx():
+    """An independent implementation (networkx, dangling mass spread evenly
+    as here) on simple directed and undirected graphs."""
+    nx = pytest.importorskip("networkx")
+    for seed, directed in ((1, True), (2, False), (3, True)):
+        g = gg.random_small(60, 0.08, seed=seed, directed=directed)
+        G = nx.DiGraph()
+        G.add_nodes_from(range(g.n))
+        deg = np.diff(g.offsets).astype(np.int64)
+        G.add_edges_from(zip(np.repeat(np.arange(g.n), deg).tolist(), g.cols.astype(np.int64).tolist()))
+        ref = nx.pagerank(G, alpha=0.85, tol=1e-14, max_iter=10000)
+        r, _ = oracle.pagerank_g(g, 0.85, tol=1e-15, max_iter=10000)
+        assert np.allclose(r, [ref[v] for v in range(g.n)], rtol=0, atol=1e-10)
+
+
 MUTANTS = [
     ("bfs level step", "level[u] = level[v] + 1;", "level[u] = level[v] + 2;"),
     ("bfs stack order", "uint64_t v = queue[head++];", "uint64_t v = queue[--tail];"),
@@ -386,6 +458,13 @@ MUTANTS = [
     ("cc link direction", "if (a < b) parent[b] = a; else parent[a] = b;",
      "if (a < b) parent[a] = b; else parent[b] = a;"),
     ("cc links a non-root", "b = uf_find(parent, cols[i]);", "b = cols[i];"),
+    ("pagerank drops dangling mass", "if (offsets[v + 1] == offsets[v]) dangling += rank[v];",
+     "if (offsets[v + 1] == offsets[v]) dangling += 0.0;"),
+    ("pagerank damps the teleport", "(1.0 - damping) / (double)n + damping * dangling",
+     "damping / (double)n + damping * dangling"),
+    ("pagerank divides by n, not the degree", "damping * rank[v] / (double)deg;",
+     "damping * rank[v] / (double)n;"),
+    ("pagerank sends to the source", "next[cols[i]] += damping", "next[v] += damping"),
 ]
 
 
@@ -399,6 +478,7 @@ def _pin_suite_fails(lib_path):
         check_invariants(impl, g, [gg.max_degree_vertex(g)])
         g = gg.uniform(1 << 12, 4, seed=3, weights=True)
         check_invariants(impl, g, [int(x) for x in gg.random_sources(g, 2, seed=2)])
+        check_pagerank(impl)
     except AssertionError:
         return True
     return False
