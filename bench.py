@@ -394,8 +394,8 @@ def ours(args):
 
     # ---- multi-source BFS, batched many-graph BFS and serving (rank 0)
     if rank == 0 and not args.no_extras:
-        for name, fn in (("kron16_bfs", extra_kron16), ("msbfs", extra_msbfs), ("batch", extra_batch),
-                         ("serving", extra_serving)):
+        for name, fn in (("kron16_bfs", extra_kron16), ("pagerank", lambda E_, t_: extra_pagerank(E_, t_, g)),
+                         ("msbfs", extra_msbfs), ("batch", extra_batch), ("serving", extra_serving)):
             try:
                 result[name] = fn(E, torch)
             except Exception as ex:  # noqa: BLE001 - report, keep the bench line
@@ -443,6 +443,25 @@ def extra_kron16(E, torch):
             ms /= reps
             res[place] = {"ms": round(ms, 4), "gteps": round(stats[-1]["edges_reached"] / (ms * 1e-3) / 1e9, 3),
                           "levels": stats[-1]["iterations"]}
+    return res
+
+
+def extra_pagerank(E, torch, g):
+    """PageRank (20 iterations, damping 0.85, no early stop) on the bench graph
+    with its edge list in pinned host memory: the whole uint64 edge list is
+    read once per iteration, so the link bound is 8 B x m per iteration."""
+    st = torch.cuda.Stream()
+    out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+    res = {"workload": f"uniform n={g.n} m={g.m}, 20 power iterations, host placement"}
+    for ids32 in (False, True):
+        with E.load_graph(g, placement="host", with_weights=False, ids32=ids32) as h:
+            E.pagerank(h, 0.85, tol=0.0, max_iters=2, out=out, stream=st)
+            _, s = E.pagerank(h, 0.85, tol=0.0, max_iters=20, out=out, stream=st, time_kernels=True)
+            per_it = s["ms"] / s["iterations"]
+            idb = 4 if ids32 else 8
+            res["ids32" if ids32 else "ids64"] = {
+                "ms_per_iteration": round(per_it, 3), "gteps": round(g.m / (per_it * 1e-3) / 1e9, 2),
+                "link_gbs_useful": round(idb * s["edges_scanned"] / (s["expand_ms"] * 1e-3) / 1e9, 1)}
     return res
 
 

@@ -223,6 +223,26 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
  * the errors of emogi_bfs. */
 emogi_status emogi_cc(emogi_graph g, uint32_t* label, const emogi_opts* opts, emogi_stats* stats);
 
+/* PageRank (the fourth application of Sec. 5.4; every vertex is active in
+ * every iteration and the whole edge list is read), by power iteration in
+ * double precision: starting from 1/n, each iteration gives every vertex
+ *   (1 - damping)/n + damping * D/n + damping * sum over edges u -> v of rank(u)/outdeg(u),
+ * where D is the rank held by vertices without out-edges, and stops after
+ * max_iters iterations or once the L1 change of an iteration is below
+ * tolerance.  Parallel edges and self-loops count as edges.  Undirected graphs
+ * are pulled (a vertex sums its own list, no atomics); directed graphs are
+ * pushed along out-edges with atomic adds.  The result equals the definition
+ * up to the order of floating-point additions.
+ *   damping    in [0, 1)
+ *   tolerance  >= 0 (0: run exactly max_iters iterations)
+ *   max_iters  >= 1
+ *   rank       double[n] output (host, or device if opts->out_on_device)
+ *   stats->iterations = iterations run; edges_reached = m * iterations.
+ * Errors: EMOGI_E_ARG (damping, tolerance, max_iters, NULL output), and the
+ * errors of emogi_bfs. */
+emogi_status emogi_pagerank(emogi_graph g, double damping, double tolerance, uint32_t max_iters, double* rank,
+                            const emogi_opts* opts, emogi_stats* stats);
+
 /* Multi-source BFS: k independent BFS traversals (1 <= k <= 64) in one
  * level-synchronous pass.  Each vertex carries 64-bit masks (visited, in the
  * frontier, reached this level), bit b for source b, so one read of a

@@ -168,6 +168,11 @@ void release_workspace(emogi_graph g) {
     dev_free(ws.lq_v, ws.lq_cap * 4);
     dev_free(ws.lq_base, ws.lq_cap * 8);
     dev_free(ws.lq_state, ws.lq_cap * 8);
+    dev_free(ws.pr_rank, ws.n * 8);
+    dev_free(ws.pr_contrib, ws.n * 8);
+    dev_free(ws.pr_acc, ws.n * 8);
+    dev_free(ws.pr_ctr, 64);
+    if (ws.h_pr_ctr) cudaFreeHost(ws.h_pr_ctr);
     dev_free(ws.ms_visit, ws.n * 8);
     dev_free(ws.ms_front, ws.n * 8);
     dev_free(ws.ms_next, ws.n * 8);

@@ -94,6 +94,12 @@ struct Workspace {
     unsigned long long* ms_next = nullptr;   // sources reaching v in the sweep under way
     uint32_t* ms_out = nullptr;              // k x n levels when the output is on the host
     size_t ms_out_bytes = 0;
+    // PageRank state, allocated on first use
+    double* pr_rank = nullptr;               // ranks when the output is on the host
+    double* pr_contrib = nullptr;            // rank / out-degree
+    double* pr_acc = nullptr;                // sums of the incoming contributions
+    void* pr_ctr = nullptr;                  // dev::PrCounters
+    void* h_pr_ctr = nullptr;                // pinned mirror
     // device-driven SSSP loop: its state block and its recorded CUDA graph
     void* sssp_loop = nullptr;               // dev::SsspLoop in device memory
     void* h_sssp_loop = nullptr;             // pinned staging copy

@@ -1304,6 +1304,200 @@ __global__ void k_sssp_loop_control(SsspLoop* Lp, Ctr* ctr, cudaGraphConditional
     cudaGraphSetConditional(handle, L.mode != 2 ? 1u : 0u);
 }
 
+// ------------------------------------------------------------------ PageRank
+// The fourth application of Sec. 5.4: every vertex is active in every
+// iteration and the whole edge list is read.  Power iteration in double
+// precision: rank'(v) = (1 - d)/n + d * dangling/n + d * sum of contrib(u)
+// over the edges u -> v, with contrib(u) = rank(u) / outdeg(u) and dangling
+// the rank held by vertices without out-edges.
+struct PrCounters {
+    double change;        // L1 change of the iteration (sum of |rank' - rank|)
+    double dangling[2];   // rank on vertices without out-edges, by iteration parity
+    double pad;
+};
+
+// List loads without weights, for the PageRank kernels.
+struct PrLoads {
+    static constexpr bool kWeights = false;
+};
+
+template <int E>
+__device__ __forceinline__ double pr_sum_step(const double* contrib, const PairLoad& p) {
+    double x = 0.0;
+    if (p.valid & 1u) x += contrib[(uint32_t)p.id.x];
+    if (p.valid & 2u) x += contrib[(uint32_t)p.id.y];
+    return x;
+}
+template <int E>
+__device__ __forceinline__ double pr_sum_step(const double* contrib, const QuadLoad& p) {
+    double x = 0.0;
+    if (p.valid & 1u) x += contrib[p.id.x];
+    if (p.valid & 2u) x += contrib[p.id.y];
+    if (p.valid & 4u) x += contrib[p.id.z];
+    if (p.valid & 8u) x += contrib[p.id.w];
+    return x;
+}
+
+// Pull form for undirected graphs (a vertex's list is also its in-list):
+// acc[v] = sum of contrib over v's list, G lanes per list in aligned 16-byte
+// steps, the group's partial sums added by a shuffle tree and stored by its
+// first lane; lists longer than large_lines go to the split queue (their
+// items add into acc[v], which the previous finalize left at 0).  No atomics
+// on the common path.
+template <int G, class Id = uint64_t>
+__global__ void __launch_bounds__(256) k_pr_pull(Sweep c, const double* contrib, double* acc) {
+    constexpr int GPW = 32 / G, E = IdWidth<Id>::kPerStep, LINE = IdWidth<Id>::kPerLine;
+    const uint32_t lane = threadIdx.x & 31u, glane = lane % G, grp = lane / G;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t n = c.all_n;
+    unsigned long long scanned = 0;
+    for (uint64_t base = warp * GPW; base < n; base += nwarps * GPW) {
+        const uint64_t v = base + grp;
+        uint64_t s = 0, e = 0;
+        if (v < n) {
+            s = c.off[v];
+            e = c.off[v + 1];
+        }
+        uint64_t a = aligned_start<Id>(s, c.shift);
+        const uint64_t lines = e > s ? (e - a + LINE - 1) / LINE : 0;
+        if (glane == 0) scanned += e - s;
+        const bool split = lines > c.large_lines;
+        if (split) {
+            if (glane == 0) defer(c, (uint32_t)v, (lines + c.chunk_lines - 1) / c.chunk_lines, 0ull);
+            s = e = a = 0;
+        }
+        const uint32_t steps = e > s ? (uint32_t)((e - a + E * G - 1) / (E * G)) : 0u;
+        const uint32_t maxsteps = __reduce_max_sync(0xffffffffu, steps);
+        double sum = 0.0;
+        for (uint32_t t = 0; t < maxsteps; t++)
+            sum += pr_sum_step<E>(contrib, load_step<PrLoads, Id>(c, a + (uint64_t)t * (E * G) + E * glane, s, e,
+                                                                  t < steps));
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (glane == 0 && v < n && !split) acc[v] = sum;
+    }
+    add_scanned(c, scanned);
+}
+
+// The split lists of k_pr_pull: one warp per item, its sum added into acc[v].
+template <class Id = uint64_t>
+__global__ void __launch_bounds__(256) k_pr_pull_split(Sweep c, const double* contrib, double* acc) {
+    constexpr int E = IdWidth<Id>::kPerStep, LINE = IdWidth<Id>::kPerLine;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long tot = *c.large;
+    const uint32_t nslots = (uint32_t)(tot >> SLOT_SHIFT);
+    const unsigned long long nitems = tot & CHUNK_MASK;
+    for (unsigned long long item = warp; item < nitems; item += nwarps) {
+        uint32_t lo = 0, hi = nslots;  // last slot whose base <= item
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (c.lq_base[mid] <= item) lo = mid; else hi = mid;
+        }
+        const uint32_t v = c.lq_v[lo];
+        const unsigned long long ci = item - c.lq_base[lo];
+        const uint64_t s = c.off[v], e = c.off[v + 1];
+        const uint64_t a = aligned_start<Id>(s, c.shift);
+        const uint64_t cs = a + ci * (uint64_t)LINE * c.chunk_lines;
+        uint64_t ce = cs + (uint64_t)LINE * c.chunk_lines;
+        if (ce > e) ce = e;
+        double sum = 0.0;
+        for (uint64_t j0 = cs; j0 < ce; j0 += 32 * E)
+            sum += pr_sum_step<E>(contrib, load_step<PrLoads, Id>(c, j0 + E * lane, s, ce, true));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) atomicAdd(acc + v, sum);
+    }
+}
+
+// Push form for directed graphs (only out-lists are stored): every edge
+// v -> u adds contrib(v) into acc[u].  The per-vertex value is the bit
+// pattern of contrib(v) (vertices without out-edges are skipped).
+struct PrPushOp {
+    const double* contrib;
+    double* acc;
+    using S = unsigned long long;
+    static constexpr S kSkip = ~0ull;
+    static constexpr bool kWeights = false;
+    static constexpr bool kPush = false;
+    static constexpr int kSteps = 1;
+    static constexpr bool kPeek = false;
+    __device__ __forceinline__ S begin(uint32_t v) {
+        const double x = contrib[v];
+        return x > 0.0 ? (S)__double_as_longlong(x) : kSkip;
+    }
+    __device__ __forceinline__ uint32_t peek(uint64_t) const { return 0; }
+    __device__ __forceinline__ bool visit(S st, uint32_t, uint64_t u, uint32_t, uint32_t) {
+        atomicAdd(acc + (uint32_t)u, __longlong_as_double((long long)st));
+        return false;
+    }
+    __device__ __forceinline__ void flush() {}
+};
+
+__device__ __forceinline__ double block_sum(double x) {
+    __shared__ double part[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5;
+    if (lane == 0) part[wid] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (uint32_t i = 0; i < (blockDim.x >> 5); i++) t += part[i];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// Iteration 0: rank = 1/n, contrib = rank / outdeg, and the dangling rank.
+static __global__ void k_pr_init(uint64_t n, const uint64_t* off, double* rank, double* contrib, PrCounters* pc) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    const double r0 = 1.0 / (double)n;
+    double dang = 0.0;
+    for (uint64_t base = tid - threadIdx.x; base < n; base += nt) {  // same trip count in a block
+        const uint64_t v = base + threadIdx.x;
+        if (v < n) {
+            const uint64_t deg = off[v + 1] - off[v];
+            rank[v] = r0;
+            contrib[v] = deg ? r0 / (double)deg : 0.0;
+            if (!deg) dang += r0;
+        }
+    }
+    const double t = block_sum(dang);
+    if (threadIdx.x == 0 && t != 0.0) atomicAdd(&pc->dangling[0], t);
+}
+
+// End of iteration `it`: rank' = base + d * acc, with base from the dangling
+// rank of this iteration; the L1 change and the next dangling rank are summed
+// per block; contrib is refreshed and acc cleared for the next iteration.
+static __global__ void k_pr_finalize(uint64_t n, const uint64_t* off, double* rank, double* contrib, double* acc,
+                                     PrCounters* pc, double damping, uint32_t it) {
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
+    const double base = (1.0 - damping) / (double)n + damping * pc->dangling[it & 1] / (double)n;
+    double chg = 0.0, dang = 0.0;
+    for (uint64_t b = tid - threadIdx.x; b < n; b += nt) {  // same trip count in a block
+        const uint64_t v = b + threadIdx.x;
+        if (v < n) {
+            const double r = base + damping * acc[v];
+            chg += fabs(r - rank[v]);
+            rank[v] = r;
+            acc[v] = 0.0;
+            const uint64_t deg = off[v + 1] - off[v];
+            contrib[v] = deg ? r / (double)deg : 0.0;
+            if (!deg) dang += r;
+        }
+    }
+    const double tc = block_sum(chg);
+    const double td = block_sum(dang);
+    if (threadIdx.x == 0) {
+        if (tc != 0.0) atomicAdd(&pc->change, tc);
+        if (td != 0.0) atomicAdd(&pc->dangling[(it + 1) & 1], td);
+    }
+}
+
 // ------------------------------------------------------------------ small kernels
 // state[v] = INF for all v, except state[src] = 0; queue = {src}.
 static __global__ void k_init_single(uint32_t* state, uint32_t n, uint32_t src, uint32_t* q, uint32_t* flag,

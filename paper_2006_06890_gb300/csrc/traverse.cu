@@ -776,6 +776,106 @@ emogi_status emogi_msbfs(emogi_graph g, const uint64_t* srcs, uint32_t k, uint32
     return EMOGI_OK;
 }
 
+emogi_status emogi_pagerank(emogi_graph g, double damping, double tolerance, uint32_t max_iters, double* rank,
+                            const emogi_opts* opts, emogi_stats* stats) {
+    clear_error();
+    Ctx c;
+    EMOGI_TRY(setup(g, opts, &c));
+    if (!(damping >= 0.0 && damping < 1.0)) return fail(EMOGI_E_ARG, "damping %g is not in [0, 1)", damping);
+    if (!(tolerance >= 0.0)) return fail(EMOGI_E_ARG, "tolerance %g is negative", tolerance);
+    if (max_iters < 1) return fail(EMOGI_E_ARG, "max_iters must be at least 1");
+    EMOGI_TRY(check_output(g, c.o, rank));
+    Workspace& ws = g->ws;
+    const uint64_t n = g->n;
+    if (!ws.pr_contrib) {
+        EMOGI_TRY(dev_alloc((void**)&ws.pr_contrib, n * 8, "PageRank contributions"));
+        EMOGI_TRY(dev_alloc((void**)&ws.pr_acc, n * 8, "PageRank sums"));
+        EMOGI_TRY(dev_alloc(&ws.pr_ctr, 64, "PageRank counters"));
+        EMOGI_CUDA_TRY(cudaHostAlloc(&ws.h_pr_ctr, 64, cudaHostAllocDefault));
+        EMOGI_CUDA_TRY(cudaMemset(ws.pr_acc, 0, n * 8));
+    }
+    double* r = rank;
+    if (!c.o.out_on_device) {
+        if (!ws.pr_rank) EMOGI_TRY(dev_alloc((void**)&ws.pr_rank, n * 8, "PageRank ranks"));
+        r = ws.pr_rank;
+    }
+    dev::PrCounters* pc = (dev::PrCounters*)ws.pr_ctr;
+    dev::PrCounters* hpc = (dev::PrCounters*)ws.h_pr_ctr;
+    const bool pull = g->flags & EMOGI_LOAD_UNDIRECTED;
+    EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[0], c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(ws.ctr, 0, sizeof(DevCounters), c.st));
+    EMOGI_CUDA_TRY(cudaMemsetAsync(pc, 0, sizeof(dev::PrCounters), c.st));
+    uint32_t it = 0;
+    if (n) {
+        dev::k_pr_init<<<grid_for(c, n), kThreads, 0, c.st>>>(n, g->d_off, r, ws.pr_contrib, pc);
+        EMOGI_CUDA_TRY(cudaGetLastError());
+        c.kernel_launches++;
+        for (; it < max_iters; it++) {
+            EMOGI_TRY(reset_sweep_counters(c, 0));
+            Sweep s = make_sweep(c, 0, true);
+            const bool timed = c.o.flags & EMOGI_OPT_TIME_KERNELS;
+            if (pull) {
+                if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[2], c.st));
+                const int grid = grid_for(c, n * c.G);
+                if (g->id_bytes == 4) {
+                    switch (c.G) {
+                        case 4: dev::k_pr_pull<4, uint32_t><<<grid, kThreads, 0, c.st>>>(s, ws.pr_contrib, ws.pr_acc); break;
+                        case 8: dev::k_pr_pull<8, uint32_t><<<grid, kThreads, 0, c.st>>>(s, ws.pr_contrib, ws.pr_acc); break;
+                        case 16: dev::k_pr_pull<16, uint32_t><<<grid, kThreads, 0, c.st>>>(s, ws.pr_contrib, ws.pr_acc); break;
+                        default: dev::k_pr_pull<32, uint32_t><<<grid, kThreads, 0, c.st>>>(s, ws.pr_contrib, ws.pr_acc); break;
+                    }
+                    dev::k_pr_pull_split<uint32_t><<<c.sms * 4, kThreads, 0, c.st>>>(s, ws.pr_contrib, ws.pr_acc);
+                } else {
+                    switch (c.G) {
+                        case 4: dev::k_pr_pull<4, uint64_t><<<grid, kThreads, 0, c.st>>>(s, ws.pr_contrib, ws.pr_acc); break;
+                        case 8: dev::k_pr_pull<8, uint64_t><<<grid, kThreads, 0, c.st>>>(s, ws.pr_contrib, ws.pr_acc); break;
+                        case 16: dev::k_pr_pull<16, uint64_t><<<grid, kThreads, 0, c.st>>>(s, ws.pr_contrib, ws.pr_acc); break;
+                        default: dev::k_pr_pull<32, uint64_t><<<grid, kThreads, 0, c.st>>>(s, ws.pr_contrib, ws.pr_acc); break;
+                    }
+                    dev::k_pr_pull_split<uint64_t><<<c.sms * 4, kThreads, 0, c.st>>>(s, ws.pr_contrib, ws.pr_acc);
+                }
+                EMOGI_CUDA_TRY(cudaGetLastError());
+                if (timed) EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[3], c.st));
+                c.kernel_launches += 2;
+                c.expand_launches++;
+            } else {
+                EMOGI_TRY(sweep(c, s, dev::PrPushOp{ws.pr_contrib, ws.pr_acc}, n));
+            }
+            EMOGI_CUDA_TRY(cudaMemsetAsync(&pc->change, 0, sizeof(double), c.st));
+            EMOGI_CUDA_TRY(cudaMemsetAsync(&pc->dangling[(it + 1) & 1], 0, sizeof(double), c.st));
+            dev::k_pr_finalize<<<grid_for(c, n), kThreads, 0, c.st>>>(n, g->d_off, r, ws.pr_contrib, ws.pr_acc, pc,
+                                                                      damping, it);
+            EMOGI_CUDA_TRY(cudaGetLastError());
+            c.kernel_launches++;
+            EMOGI_CUDA_TRY(cudaMemcpyAsync(hpc, pc, sizeof(dev::PrCounters), cudaMemcpyDeviceToHost, c.st));
+            EMOGI_TRY(read_counters(c));
+            if (hpc->change < tolerance) {
+                it++;
+                break;
+            }
+        }
+    }
+    EMOGI_CUDA_TRY(cudaEventRecord(ws.ev[1], c.st));
+    if (!c.o.out_on_device && n)
+        EMOGI_CUDA_TRY(cudaMemcpyAsync(rank, r, n * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    EMOGI_CUDA_TRY(cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c.st));
+    EMOGI_CUDA_TRY(cudaStreamSynchronize(c.st));
+    if (stats) {
+        float ms = 0.f;
+        EMOGI_CUDA_TRY(cudaEventElapsedTime(&ms, ws.ev[0], ws.ev[1]));
+        memset(stats, 0, sizeof *stats);
+        stats->iterations = it;
+        stats->edges_scanned = ws.h_ctr->scanned;
+        stats->edges_reached = g->m * (uint64_t)it;
+        stats->edge_bytes = ws.h_ctr->scanned * g->id_bytes;
+        stats->ms = ms;
+        stats->expand_ms = c.expand_ms;
+        stats->expand_launches = c.expand_launches;
+        stats->kernel_launches = c.kernel_launches;
+    }
+    return EMOGI_OK;
+}
+
 emogi_status emogi_cc(emogi_graph g, uint32_t* label, const emogi_opts* opts, emogi_stats* stats) {
     clear_error();
     Ctx c;

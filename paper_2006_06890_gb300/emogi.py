@@ -77,6 +77,8 @@ _SIGNATURES = [
     ("emogi_bfs", _I32, [_P, _U64, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
     ("emogi_sssp", _I32, [_P, _U64, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
     ("emogi_cc", _I32, [_P, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
+    ("emogi_pagerank", _I32, [_P, ctypes.c_double, ctypes.c_double, _U32, _P, ctypes.POINTER(Opts),
+                              ctypes.POINTER(Stats)]),
     ("emogi_msbfs", _I32, [_P, _P, _U32, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
     ("emogi_set_device_budget", _I32, [_U64]),
     ("emogi_device_bytes_in_use", _U64, []),
@@ -315,6 +317,27 @@ def sssp(g: Graph, src: int, out=None, **kw):
 def cc(g: Graph, out=None, **kw):
     """emogi_cc -> (label array, stats dict)."""
     return _run(lib().emogi_cc, g, (), out, kw)
+
+
+def pagerank(g: Graph, damping=0.85, tol=1e-10, max_iters=100, out=None, **kw):
+    """emogi_pagerank -> (float64 ranks, stats dict); `out` may be a float64
+    numpy array or a CUDA float64 tensor of n entries."""
+    if out is None:
+        arr = np.empty(max(g.n, 1), dtype=np.float64)
+        ptr, res, on_dev = arr.ctypes.data, arr[:g.n], False
+    elif hasattr(out, "data_ptr"):
+        if out.numel() < g.n or out.element_size() != 8 or not out.is_contiguous():
+            raise EmogiError(E_ARG, "output tensor must be contiguous float64 with n entries")
+        ptr, res, on_dev = out.data_ptr(), out, bool(out.is_cuda)
+    else:
+        if out.dtype != np.float64 or out.size < g.n or not out.flags.c_contiguous:
+            raise EmogiError(E_ARG, "output array must be contiguous float64 with n entries")
+        ptr, res, on_dev = out.ctypes.data, out, False
+    o = _opts(out_on_device=on_dev, **kw)
+    s = Stats()
+    _check(lib().emogi_pagerank(g.handle, float(damping), float(tol), int(max_iters), ptr, ctypes.byref(o),
+                                ctypes.byref(s)))
+    return res, s.as_dict()
 
 
 def msbfs(g: Graph, sources, out=None, **kw):
