@@ -56,10 +56,11 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the multi-source, batched and serving measurements")
     ap.add_argument("--ncu-case", nargs="?", const="traversal", default=None,
-                    choices=["traversal", "msbfs", "batch"],
+                    choices=["traversal", "msbfs", "batch", "pagerank"],
                     help="profiling case, then exit: 'traversal' = one BFS, SSSP and CC on a 2^22-vertex uniform "
                          "graph (1.1 GB edges in pinned host memory); 'msbfs' = one 64-source pass on a scale-22 "
-                         "Kronecker graph in host memory; 'batch' = one batched BFS over 128 uneven graphs in HBM")
+                         "Kronecker graph in host memory; 'batch' = one batched BFS over 128 uneven graphs in HBM; "
+                         "'pagerank' = 3 PageRank iterations on the 2^22-vertex uniform graph in host memory")
     return ap.parse_args()
 
 
@@ -686,6 +687,13 @@ def ncu_case(args):
         with E.load_graph(g, placement="host") as h:
             st = E.msbfs(h, srcs, out=out)[1]
         print(json.dumps({"ncu_case": "msbfs Kronecker scale 22 ef 16, 64 sources, host", "stats": st}))
+        return
+    if args.ncu_case == "pagerank":
+        g, _ = make_graph(1 << 22, args.degree)
+        out = torch.empty(g.n, dtype=torch.float64, device="cuda")
+        with E.load_graph(g, placement="host", with_weights=False) as h:
+            st = E.pagerank(h, 0.85, tol=0.0, max_iters=3, out=out)[1]
+        print(json.dumps({"ncu_case": f"PageRank, 3 iterations, uniform n=2^22 degree {args.degree}, host", "stats": st}))
         return
     if args.ncu_case == "batch":
         rng = np.random.default_rng(4)
