@@ -1370,9 +1370,16 @@ __global__ void __launch_bounds__(256) k_pr_pull(Sweep c, const double* contrib,
         const uint32_t steps = e > s ? (uint32_t)((e - a + E * G - 1) / (E * G)) : 0u;
         const uint32_t maxsteps = __reduce_max_sync(0xffffffffu, steps);
         double sum = 0.0;
-        for (uint32_t t = 0; t < maxsteps; t++)
-            sum += pr_sum_step<E>(contrib, load_step<PrLoads, Id>(c, a + (uint64_t)t * (E * G) + E * glane, s, e,
-                                                                  t < steps));
+        // the loads of KS steps go out before their contributions are gathered
+        constexpr int KS = E == 2 ? 4 : 2;
+        for (uint32_t t0 = 0; t0 < maxsteps; t0 += KS) {
+            typename StepOf<Id>::T p[KS];
+#pragma unroll
+            for (int u = 0; u < KS; u++)
+                p[u] = load_step<PrLoads, Id>(c, a + (uint64_t)(t0 + u) * (E * G) + E * glane, s, e, t0 + u < steps);
+#pragma unroll
+            for (int u = 0; u < KS; u++) sum += pr_sum_step<E>(contrib, p[u]);
+        }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if (glane == 0 && v < n && !split) acc[v] = sum;
@@ -1404,8 +1411,14 @@ __global__ void __launch_bounds__(256) k_pr_pull_split(Sweep c, const double* co
         uint64_t ce = cs + (uint64_t)LINE * c.chunk_lines;
         if (ce > e) ce = e;
         double sum = 0.0;
-        for (uint64_t j0 = cs; j0 < ce; j0 += 32 * E)
-            sum += pr_sum_step<E>(contrib, load_step<PrLoads, Id>(c, j0 + E * lane, s, ce, true));
+        constexpr int KS = E == 2 ? 4 : 2;
+        for (uint64_t j0 = cs; j0 < ce; j0 += 32 * E * KS) {
+            typename StepOf<Id>::T p[KS];
+#pragma unroll
+            for (int u = 0; u < KS; u++) p[u] = load_step<PrLoads, Id>(c, j0 + 32 * E * u + E * lane, s, ce, true);
+#pragma unroll
+            for (int u = 0; u < KS; u++) sum += pr_sum_step<E>(contrib, p[u]);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if (lane == 0) atomicAdd(acc + v, sum);
