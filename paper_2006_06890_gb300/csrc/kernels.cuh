@@ -54,6 +54,8 @@ struct Sweep {
     uint32_t chunk_lines = 1;            // lines per split work item
     unsigned long long* scanned = nullptr;         // neighbour entries read (statistics)
     const uint32_t* heads = nullptr;     // first kHeads ids of every list in GPU memory, or null
+    uint64_t m = 0;                      // entries in the edge list (and weights): a lane's 16-byte
+                                         // load at index j is whole when j + ids per load <= m
 };
 
 // Entries of each list mirrored in GPU memory ("list heads", INF-padded).
@@ -335,6 +337,52 @@ struct SsspOpT {
         fflag[u] = 1u;  // idempotent: the split scans the flags, no queue to append to
         return false;
     }
+    // The relaxations of one load step (N entries of a lane) taken together:
+    // every improving entry's atomicMin is issued before any result is used,
+    // then the round stamps of those that improved, so a lane waits for two
+    // L2 round trips per step rather than two per entry.  Same outcome as N
+    // calls of visit() in entry order: atomics on one address stay in program
+    // order, and min / max commute across addresses.
+#ifndef EMOGI_SSSP_BATCHED_RELAX
+#define EMOGI_SSSP_BATCHED_RELAX 1
+#endif
+    static constexpr bool kVisitN = EMOGI_SSSP_BATCHED_RELAX != 0;
+    template <int N>
+    __device__ __forceinline__ void visit_n(uint32_t dv, const uint32_t (&u)[N], const uint32_t (&w)[N],
+                                            const uint32_t (&cur)[N], uint32_t valid, bool (&push)[N]) {
+        uint32_t nd[N];
+        bool go[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            const uint64_t nd64 = (uint64_t)dv + (uint64_t)w[i];
+            const bool in = (valid >> i) & 1u;
+            if (in && nd64 >= (uint64_t)INF && dv != INF) atomicExch(overflow, 1u);
+            nd[i] = (uint32_t)nd64;
+            go[i] = in && nd64 < (uint64_t)INF && nd[i] < cur[i];
+        }
+        uint32_t old[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) old[i] = go[i] ? atomicMin(dist + u[i], nd[i]) : 0u;
+        bool near[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            const bool better = go[i] && nd[i] < old[i];
+            near[i] = better && nd[i] < T;
+            if (better && !near[i]) {
+                lmin = nd[i] < lmin ? nd[i] : lmin;
+                fflag[u[i]] = 1u;
+            }
+        }
+        uint32_t stamp[N];
+#pragma unroll
+        for (int i = 0; i < N; i++) stamp[i] = near[i] ? atomicMax(qround + u[i], round + 1) : round + 1;
+#pragma unroll
+        for (int i = 0; i < N; i++) {
+            const bool fresh = near[i] && stamp[i] < round + 1;
+            if (kFlags && fresh) nflag[u[i]] = 1;
+            push[i] = !kFlags && fresh;
+        }
+    }
     __device__ __forceinline__ void flush() { warp_atomic_min(far_min, lmin); }
 };
 using SsspOp = SsspOpT<false>;
@@ -506,6 +554,12 @@ struct QuadLoad {
 template <class Id> struct StepOf { using T = PairLoad; };
 template <> struct StepOf<uint32_t> { using T = QuadLoad; };
 
+// A list's last load, which may hold ids of the next list, is a whole
+// 16-byte load (its extra ids masked off) unless it would pass the end of the
+// edge list; element loads there cost up to three more requests per lane.
+#ifndef EMOGI_WHOLE_TAIL_LOADS
+#define EMOGI_WHOLE_TAIL_LOADS 0
+#endif
 template <class Op>
 __device__ __forceinline__ PairLoad load_pair(const Sweep& c, uint64_t j, uint64_t s, uint64_t e, bool active) {
     const uint64_t* cols = (const uint64_t*)c.cols;
@@ -514,10 +568,10 @@ __device__ __forceinline__ PairLoad load_pair(const Sweep& c, uint64_t j, uint64
     p.w = make_uint2(0, 0);
     p.valid = 0;
     if (active && j + 1 >= s) {
-        if (j + 1 < e) {
+        if (j + 1 < e || (EMOGI_WHOLE_TAIL_LOADS && j < e && j + 2 <= c.m)) {
             p.id = ld_edge2(cols + j);
             if (Op::kWeights) p.w = ld_w2(c.w + j);
-            p.valid = (j >= s ? 1u : 0u) | 2u;
+            p.valid = (j >= s ? 1u : 0u) | (j + 1 < e ? 2u : 0u);
         } else if (j < e && j >= s) {
             p.id.x = ld_edge(cols + j);
             if (Op::kWeights) p.w.x = ld_w(c.w + j);
@@ -535,11 +589,12 @@ __device__ __forceinline__ QuadLoad load_quad(const Sweep& c, uint64_t j, uint64
     p.w = make_uint4(0, 0, 0, 0);
     p.valid = 0;
     if (active && j + 3 >= s && j < e) {
-        if (j + 3 < e) {
+        if (j + 3 < e || (EMOGI_WHOLE_TAIL_LOADS && j + 4 <= c.m)) {
             p.id = ld_u32x4(cols + j);
             if (Op::kWeights) p.w = ld_u32x4(c.w + j);
-            p.valid = (j >= s ? 1u : 0u) | (j + 1 >= s ? 2u : 0u) | (j + 2 >= s ? 4u : 0u) | 8u;
-        } else {  // the list's last step: element loads, nothing read past e
+            p.valid = (j >= s ? 1u : 0u) | (j + 1 >= s && j + 1 < e ? 2u : 0u) | (j + 2 >= s && j + 2 < e ? 4u : 0u) |
+                      (j + 3 < e ? 8u : 0u);
+        } else {  // the last load of the whole edge list: element loads, nothing read past m
             if (j >= s) {
                 p.id.x = ld_w(cols + j);
                 if (Op::kWeights) p.w.x = ld_w(c.w + j);
@@ -635,11 +690,24 @@ __device__ __forceinline__ void warpq_push4(WarpQ& wq, uint32_t* q, uint32_t* co
     wq.cnt += total;
 }
 
+// Ops with a batched visit (visit_n) declare kVisitN.
+template <class Op, class = void> struct HasVisitN { static constexpr bool value = false; };
+template <class Op> struct HasVisitN<Op, decltype((void)Op::kVisitN)> { static constexpr bool value = Op::kVisitN; };
+
 template <class Op>
 __device__ __forceinline__ void visit_step(const Sweep& c, Op& op, typename Op::S st, uint32_t v, const PairLoad& p,
                                            uint2 cur, WarpQ& wq) {
-    const bool p0 = (p.valid & 1u) && op.visit(st, v, p.id.x, p.w.x, cur.x);
-    const bool p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y, cur.y);
+    bool p0, p1;
+    if constexpr (HasVisitN<Op>::value) {
+        const uint32_t u[2] = {(uint32_t)p.id.x, (uint32_t)p.id.y}, w[2] = {p.w.x, p.w.y}, cu[2] = {cur.x, cur.y};
+        bool pu[2];
+        op.template visit_n<2>(st, u, w, cu, p.valid, pu);
+        p0 = pu[0];
+        p1 = pu[1];
+    } else {
+        p0 = (p.valid & 1u) && op.visit(st, v, p.id.x, p.w.x, cur.x);
+        p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y, cur.y);
+    }
     if (Op::kPush)
         warpq_push4(wq, c.out_q, c.out_count, p0, p1, false, false,
                     make_uint4((uint32_t)p.id.x, (uint32_t)p.id.y, 0u, 0u));
@@ -647,10 +715,22 @@ __device__ __forceinline__ void visit_step(const Sweep& c, Op& op, typename Op::
 template <class Op>
 __device__ __forceinline__ void visit_step(const Sweep& c, Op& op, typename Op::S st, uint32_t v, const QuadLoad& p,
                                            uint4 cur, WarpQ& wq) {
-    const bool p0 = (p.valid & 1u) && op.visit(st, v, p.id.x, p.w.x, cur.x);
-    const bool p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y, cur.y);
-    const bool p2 = (p.valid & 4u) && op.visit(st, v, p.id.z, p.w.z, cur.z);
-    const bool p3 = (p.valid & 8u) && op.visit(st, v, p.id.w, p.w.w, cur.w);
+    bool p0, p1, p2, p3;
+    if constexpr (HasVisitN<Op>::value) {
+        const uint32_t u[4] = {p.id.x, p.id.y, p.id.z, p.id.w}, w[4] = {p.w.x, p.w.y, p.w.z, p.w.w},
+                       cu[4] = {cur.x, cur.y, cur.z, cur.w};
+        bool pu[4];
+        op.template visit_n<4>(st, u, w, cu, p.valid, pu);
+        p0 = pu[0];
+        p1 = pu[1];
+        p2 = pu[2];
+        p3 = pu[3];
+    } else {
+        p0 = (p.valid & 1u) && op.visit(st, v, p.id.x, p.w.x, cur.x);
+        p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y, cur.y);
+        p2 = (p.valid & 4u) && op.visit(st, v, p.id.z, p.w.z, cur.z);
+        p3 = (p.valid & 8u) && op.visit(st, v, p.id.w, p.w.w, cur.w);
+    }
     if (Op::kPush) warpq_push4(wq, c.out_q, c.out_count, p0, p1, p2, p3, p.id);
 }
 

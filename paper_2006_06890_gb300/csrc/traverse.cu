@@ -127,6 +127,7 @@ Sweep make_sweep(const Ctx& c, int side, bool all_vertices) {
     s.chunk_lines = c.chunk;
     s.scanned = &ws.ctr->scanned;
     s.heads = g->d_heads;
+    s.m = g->m;
     return s;
 }
 
