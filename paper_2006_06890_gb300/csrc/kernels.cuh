@@ -558,7 +558,7 @@ template <> struct StepOf<uint32_t> { using T = QuadLoad; };
 // 16-byte load (its extra ids masked off) unless it would pass the end of the
 // edge list; element loads there cost up to three more requests per lane.
 #ifndef EMOGI_WHOLE_TAIL_LOADS
-#define EMOGI_WHOLE_TAIL_LOADS 0
+#define EMOGI_WHOLE_TAIL_LOADS 1
 #endif
 template <class Op>
 __device__ __forceinline__ PairLoad load_pair(const Sweep& c, uint64_t j, uint64_t s, uint64_t e, bool active) {

@@ -183,3 +183,55 @@ def test_ids32_hub_larger_than_a_split_chunk():
         exp = oracle.bfs_g(g, 0)
         np.testing.assert_array_equal(E.bfs(h, 0, top_down_only=True)[0], exp)
         np.testing.assert_array_equal(E.sssp(h, 0)[0], oracle.sssp_g(g, 0))
+
+
+def array_end_graph(r, symmetric):
+    """A graph whose last list ends at the end of the edge array, with
+    m = r (mod 4) for a directed graph (every residue of a 16-byte load of
+    uint32 ids, and of uint64 ids mod 2) and m even for a symmetric one; the
+    last vertex has the longest list so that it ends in a partial load."""
+    rng = np.random.default_rng(100 + r)
+    n = 48
+    s, d = [], []
+    for v in range(n - 1):
+        for u in rng.choice(n, size=int(rng.integers(0, 6)), replace=False):
+            s.append(v)
+            d.append(int(u))
+    if symmetric:  # m is even: m = 2 (mod 4) for odd r
+        k = 30
+        while True:
+            last = [int(u) for u in rng.choice(n - 1, size=k, replace=False)]
+            g = gg.csr_from_edges(n, s + [n - 1] * k, d + last, symmetrize=True, name=f"array-end-sym{r}")
+            if g.m % 4 == 2 * (r % 2):
+                return gg.add_weights(g, seed=r)
+            k += 1
+    k = 37
+    while (len(s) + k) % 4 != r:
+        k += 1
+    last = [int(u) for u in rng.integers(0, n, size=k)]
+    s += [n - 1] * k
+    d += last
+    return gg.csr_from_edges(n, s, d, weights=rng.integers(1, 256, size=len(s)), symmetrize=False, dedup=False,
+                             drop_self_loops=False, sort=False, name=f"array-end{r}")
+
+
+@pytest.mark.parametrize("ids32", [True, False], ids=["u32", "u64"])
+@pytest.mark.parametrize("placement", ["device", "host", "managed"])
+@pytest.mark.parametrize("r", [0, 1, 2, 3])
+def test_lists_ending_at_the_end_of_the_edge_array(r, placement, ids32):
+    """The load of a list's last ids is a whole 16-byte load (ids past the
+    list masked off) except where it would pass the end of the edge array;
+    lists ending at every residue of m, and at m itself, stay exact."""
+    for symmetric in (False, True):
+        g = array_end_graph(r, symmetric)
+        assert g.offsets[-2] < g.offsets[-1] == g.m
+        with E.load_graph(g, placement=placement, ids32=ids32) as h:
+            for kw in (dict(), dict(granularity=4), dict(granularity=32)):
+                check_all(g, h, **kw)
+                for s in range(0, g.n, 7):
+                    np.testing.assert_array_equal(E.sssp(h, s, **kw)[0], oracle.sssp_g(g, s))
+            if symmetric:
+                exp, _ = oracle.pagerank_g(g, 0.85, tol=0.0, max_iter=15)
+                np.testing.assert_allclose(E.pagerank(h, 0.85, tol=0.0, max_iters=15)[0], exp, rtol=1e-9, atol=1e-12)
+                srcs = list(range(0, g.n, 3))
+                np.testing.assert_array_equal(E.msbfs(h, srcs)[0], oracle.msbfs(g.n, g.offsets, g.cols, srcs))
