@@ -1012,7 +1012,7 @@ __global__ void __launch_bounds__(256) k_bfs_bottom_up(Sweep c, uint32_t* level,
                     const uint64_t j = a + (uint64_t)t * (E * G) + E * glane;
                     if (j + E - 1 >= ss && j < ee) {
                         uint32_t id[E];
-                        if (j + E - 1 < ee) {
+                        if (j + E - 1 < ee || (EMOGI_WHOLE_TAIL_LOADS && j + E <= c.m)) {
                             ld_ids<Id>(c.cols, j, id);
                         } else {
 #pragma unroll
@@ -1757,7 +1757,7 @@ __global__ void __launch_bounds__(256) k_ms_bottom_up(Sweep c, const unsigned lo
                     const uint64_t j = a + (uint64_t)t * (E * G) + E * glane;
                     if (j + E - 1 >= ss && j < ee) {
                         uint32_t id[E];
-                        if (j + E - 1 < ee) {
+                        if (j + E - 1 < ee || (EMOGI_WHOLE_TAIL_LOADS && j + E <= c.m)) {
                             ld_ids<Id>(c.cols, j, id);
                         } else {
 #pragma unroll
