@@ -211,7 +211,7 @@ def step_alg_bytes(stats):
 # (profiles/link_traffic_per_kernel_urand22_host.md); the 32-byte sector waste
 # of lists that do not start on a sector grows with the entries read, so the
 # per-entry factor scales to the 2^24 graph.
-LINK_BYTES_PER_ALG_BYTE = {"bfs": 1.136, "sssp": 1.188, "cc": 1.0}
+LINK_BYTES_PER_ALG_BYTE = {"bfs": 1.130, "sssp": 1.135, "cc": 1.0}
 
 
 def step_link_bytes(stats):
@@ -336,7 +336,7 @@ def ours(args):
                      "frac": round(achieved / link_peak, 4),
                      "traffic": int(sum(step_link_bytes(p) for p in per) / len(per)),
                      "traffic_note": "host-link read bytes per step of the expansion kernels: ncu sysmem read "
-                                     "sectors x 32 per list entry on the 2^22 case (BFS 1.136, SSSP 1.188 per "
+                                     "sectors x 32 per list entry on the 2^22 case (BFS 1.130, SSSP 1.135 per "
                                      "algorithmic byte), scaled by this run's entries",
                      "link_frac": round(sum(step_link_bytes(p) for p in per) / (expand_ms * 1e-3) / 1e9 / link_peak, 4),
                      "peak_source": "pinned host->device cudaMemcpy, 1 GiB, best of 6, measured in this run",
