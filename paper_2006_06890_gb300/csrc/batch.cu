@@ -27,6 +27,7 @@ struct BatchGraph {
     const uint64_t* off;
     const void* cols;
     uint64_t base;   // first entry of this graph in the combined level array
+    uint64_t m;      // entries in the edge list
     uint32_t n;
     uint32_t shift;
     uint32_t ids32;  // 1: uint32 ids, 0: uint64 ids
@@ -172,7 +173,7 @@ __global__ void __launch_bounds__(256) k_batch_bfs(BatchParams p) {
             for (uint32_t c0 = base; c0 < base + step && c0 < k; c0 += GPW) {
                 const uint32_t idx = c0 + grp;
                 uint64_t s = 0, e = 0, a = 0;
-                BatchGraph d = {nullptr, nullptr, 0, 0, 0, 0, 0};
+                BatchGraph d = {nullptr, nullptr, 0, 0, 0, 0, 0, 0};
                 uint32_t v = 0, gi = 0;
                 if (idx < k && idx < base + step) {
                     const uint2 en = in_q[idx];
@@ -193,7 +194,9 @@ __global__ void __launch_bounds__(256) k_batch_bfs(BatchParams p) {
                     uint32_t u[2] = {0, 0};
                     bool ok[2] = {false, false};
                     if (t < steps && j + 1 >= s) {
-                        if (j + 1 < e) {
+                        // a list's last ids too come in one whole load, unless it would pass
+                        // the end of the edge list
+                        if (j + 1 < e || (EMOGI_WHOLE_TAIL_LOADS && j < e && j + 2 <= d.m)) {
                             if (d.ids32) {
                                 const uint2 pr = dev::ld_w2((const uint32_t*)d.cols + j);
                                 u[0] = pr.x;
@@ -204,7 +207,7 @@ __global__ void __launch_bounds__(256) k_batch_bfs(BatchParams p) {
                                 u[1] = (uint32_t)pr.y;
                             }
                             ok[0] = j >= s;
-                            ok[1] = true;
+                            ok[1] = j + 1 < e;
                         } else if (j < e && j >= s) {
                             u[0] = d.ids32 ? dev::ld_id<uint32_t>(d.cols, j) : dev::ld_id<uint64_t>(d.cols, j);
                             ok[0] = true;
@@ -421,7 +424,7 @@ emogi_status emogi_batch_create(const emogi_graph* graphs, uint32_t count, emogi
             return fail(EMOGI_E_ARG, "all graphs of a batch must be on one device");
         }
         b->base[g] = b->total;
-        table[g] = BatchGraph{gr->d_off, gr->cols, b->total, (uint32_t)gr->n, gr->shift,
+        table[g] = BatchGraph{gr->d_off, gr->cols, b->total, gr->m, (uint32_t)gr->n, gr->shift,
                               gr->id_bytes == 4 ? 1u : 0u, 0u};
         b->total += gr->n;
     }
