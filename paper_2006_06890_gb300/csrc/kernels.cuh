@@ -556,7 +556,10 @@ template <> struct StepOf<uint32_t> { using T = QuadLoad; };
 
 // A list's last load, which may hold ids of the next list, is a whole
 // 16-byte load (its extra ids masked off) unless it would pass the end of the
-// edge list; element loads there cost up to three more requests per lane.
+// edge list.  Element loads there cost up to three more requests per lane,
+// and some fetched a host sector a second time (measured on GB300, uniform
+// degree 32 from host memory: SSSP link bytes per algorithmic byte 1.188 ->
+// 1.135; SSSP 42.65 -> 40.6 ms with uint64 ids, 37.1 -> 30.1 ms with uint32).
 #ifndef EMOGI_WHOLE_TAIL_LOADS
 #define EMOGI_WHOLE_TAIL_LOADS 1
 #endif
@@ -594,7 +597,7 @@ __device__ __forceinline__ QuadLoad load_quad(const Sweep& c, uint64_t j, uint64
             if (Op::kWeights) p.w = ld_u32x4(c.w + j);
             p.valid = (j >= s ? 1u : 0u) | (j + 1 >= s && j + 1 < e ? 2u : 0u) | (j + 2 >= s && j + 2 < e ? 4u : 0u) |
                       (j + 3 < e ? 8u : 0u);
-        } else {  // the last load of the whole edge list: element loads, nothing read past m
+        } else {  // the last load of the whole edge list: element loads, nothing read at or past m
             if (j >= s) {
                 p.id.x = ld_w(cols + j);
                 if (Op::kWeights) p.w.x = ld_w(c.w + j);
