@@ -1,0 +1,104 @@
+"""Parity at the benchmark's full sizes and in the launch configuration that
+`bench.py` times (default options, device outputs written on a side stream).
+
+- Uniform n = 2^24, average degree 32 (m = 537 M ids + weights, 6.4 GB) in
+  pinned host memory, with uint64 ids and with the 4-byte edge list: BFS and
+  CC equal the oracle element by element; SSSP, whose Dijkstra takes about a
+  minute at this size, passes the shortest-distance certificate, which holds
+  exactly for the true distances (`sssp_certificate.py`).
+- Kronecker scale 24, edge factor 16, 64 sources in one multi-source pass:
+  sampled rows equal the oracle's BFS from those sources.
+- 512 uneven uniform graphs traversed in one batch after autotuning: sampled
+  graphs (the smallest, the largest and a spread between) equal the oracle.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+from sssp_certificate import sssp_certificate
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2006_06890_gb300 import emogi as E  # noqa: E402
+
+GEN_SEED, SRC_SEED = 1, 2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2006_06890_gb300 import _build
+    _build.build()
+    E.lib()
+    yield
+
+
+def host_u32(t):
+    torch.cuda.synchronize()  # the library wrote on its own or a side stream
+    return t.cpu().numpy().view(np.uint32)
+
+
+@pytest.fixture(scope="module")
+def uniform24():
+    g = gg.uniform(1 << 24, 32, seed=GEN_SEED, weights=True)
+    srcs = [int(s) for s in gg.random_sources(g, 16, seed=SRC_SEED)]
+    exp = {"bfs": oracle.bfs_g(g, srcs[0]), "cc": oracle.cc_g(g)}
+    return g, srcs, exp
+
+
+@pytest.mark.parametrize("ids32", [False, True], ids=["u64", "u32"])
+def test_uniform_2_24_host_bfs_sssp_cc(uniform24, ids32):
+    g, srcs, exp = uniform24
+    stream = torch.cuda.Stream()
+    outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(3)]
+    with E.load_graph(g, placement="host", ids32=ids32) as h:
+        kw = dict(stream=stream, time_kernels=True)
+        _, sb = E.bfs(h, srcs[0], out=outs[0], **kw)
+        np.testing.assert_array_equal(host_u32(outs[0]), exp["bfs"])
+        assert sb["edges_reached"] == oracle.reached_edges(g.offsets, exp["bfs"])
+        for s in srcs[1:2]:
+            E.sssp(h, s, out=outs[1], **kw)
+            dist = host_u32(outs[1])
+            why = sssp_certificate(g.offsets, g.cols, g.weights, s, dist)
+            assert why is None, f"sssp from {s}: {why}"
+        E.cc(h, out=outs[2], **kw)
+        np.testing.assert_array_equal(host_u32(outs[2]), exp["cc"])
+
+
+def test_kronecker_24_msbfs_64_sources_sampled_rows():
+    g = gg.kronecker(24, 16, seed=GEN_SEED)
+    srcs = [int(s) for s in gg.random_sources(g, 64, seed=SRC_SEED)]
+    stream = torch.cuda.Stream()
+    out = torch.empty((64, g.n), dtype=torch.int32, device="cuda")
+    with E.load_graph(g, placement="host") as h:
+        E.msbfs(h, srcs, out=out, stream=stream)
+        for k in (0, 31, 63):
+            row = host_u32(out[k])
+            np.testing.assert_array_equal(row, oracle.bfs_g(g, srcs[k]), err_msg=f"row {k}, source {srcs[k]}")
+
+
+def test_512_uneven_graphs_batch_sampled_graphs():
+    rng = np.random.default_rng(4)
+    gs = []
+    for i in range(512):
+        n = int(2 ** rng.uniform(10, 18))
+        gs.append(gg.uniform(n, int(rng.integers(4, 65)), seed=4000 + i))
+    srcs = [gg.max_degree_vertex(g) for g in gs]
+    sizes = np.array([g.n for g in gs])
+    pick = sorted({int(sizes.argmin()), int(sizes.argmax()), *range(0, 512, 73)})
+    hs = [E.load_graph(g, placement="device") for g in gs]
+    try:
+        with E.Batch(hs) as b:
+            b.autotune(srcs)
+            out = torch.empty(b.total, dtype=torch.int32, device="cuda")
+            levels, _ = b.bfs(srcs, out=out)
+            for i in pick:
+                np.testing.assert_array_equal(host_u32(levels[i]), oracle.bfs_g(gs[i], srcs[i]),
+                                              err_msg=f"graph {i}")
+    finally:
+        for h in hs:
+            h.free()
