@@ -72,12 +72,12 @@ struct Slot {
 
 // Device bytes a traversal handle's buffers take for a graph of n vertices
 // and m edges (two frontier queues, the state array, SSSP stamps, far flags
-// and last-expanded distances, the split-list queue, multi-source masks);
-// mirrors the library's workspace layout.
+// and last-expanded distances, the next-frontier flag bytes, the split-list
+// queue, multi-source masks); mirrors the library's workspace layout.
 uint64_t workspace_estimate(emogi_graph g) {
     const uint64_t n = g->n ? g->n : 1;
     const uint64_t lq = std::min<uint64_t>(n, g->m / 497 + 1);
-    return 6 * 4 * n + 20 * lq + 3 * 8 * n + 1024;
+    return 6 * 4 * n + (n / 16 + 1) * 16 + 20 * lq + 3 * 8 * n + 1024;
 }
 
 }  // namespace

@@ -108,7 +108,7 @@ def test_budget_limits_batches_and_rejects_what_never_fits(resident):
     g, h = gs[1], hs[1]
     n = g.n
     # room for the buffers plus about 4 level rows: batches shrink, results stay exact
-    budget = (6 * 4 * n + 20 * (g.m // 497 + 1) + 3 * 8 * n + 1024) + 4 * 4 * n + 16
+    budget = (6 * 4 * n + (n // 16 + 1) * 16 + 20 * (g.m // 497 + 1) + 3 * 8 * n + 1024) + 4 * 4 * n + 16
     srcs = [int(x) for x in gg.random_sources(g, 40, seed=6)]
     with E.Server(max_slots=2, device_budget=budget) as srv:
         outs = [np.empty(n, dtype=np.uint32) for _ in srcs]
