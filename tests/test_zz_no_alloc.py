@@ -6,7 +6,8 @@ code sharing a context whose allocator it may not use) hand the library their
 own graph and output buffers; the library keeps its frontier queues in one
 fixed array per device instead of calling cudaMalloc.  This file checks,
 through the C ABI, that two calls in a row give exactly what emogi_bfs gives.
-It is collected last so that a failure here never hides another test.
+It is collected after the other parity tests (only the full-size cases come
+later) so that a failure here hides none of them.
 """
 import numpy as np
 import pytest

@@ -1,5 +1,7 @@
 """Parity at the benchmark's full sizes and in the launch configuration that
 `bench.py` times (default options, device outputs written on a side stream).
+The file is collected last: its cases take minutes, and a failure here hides
+no other test.
 
 - Uniform n = 2^24, average degree 32 (m = 537 M ids + weights, 6.4 GB) in
   pinned host memory, with uint64 ids and with the 4-byte edge list: BFS and
