@@ -394,9 +394,12 @@ const char* emogi_version(void);
  * every GPU that loads the library holds until the process exits.
  *   n            number of vertices, 1 <= n <= EMOGI_NOALLOC_MAX_VERTICES;
  *                larger graphs are rejected with EMOGI_E_ARG
- *   row_offsets  device uint64_t[n+1] (CSR vertex list, as emogi_load_csr)
+ *   row_offsets  device uint64_t[n+1] (CSR vertex list, as emogi_load_csr);
+ *                the call reads row_offsets[n] (the edge count) once into a
+ *                host variable
  *   col_idx      uint64_t[row_offsets[n]] readable by the current device:
  *                device memory or mapped pinned host memory; 16-byte aligned
+ *                (not necessarily 128-byte aligned)
  *   src          source vertex, < n
  *   level        device uint32_t[n] output, as emogi_bfs
  *   cuda_stream  cudaStream_t to run on (NULL = the legacy default stream)

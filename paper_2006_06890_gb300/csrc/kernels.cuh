@@ -56,6 +56,8 @@ struct Sweep {
     const uint32_t* heads = nullptr;     // first kHeads ids of every list in GPU memory, or null
     uint64_t m = 0;                      // entries in the edge list (and weights): a lane's 16-byte
                                          // load at index j is whole when j + ids per load <= m
+    uint32_t qcap = 0xFFFFFFFFu;         // entries out_q holds: an append at or past it is dropped
+                                         // while the count still grows, so the host sees count > qcap
 };
 
 // Entries of each list mirrored in GPU memory ("list heads", INF-padded).
@@ -155,8 +157,9 @@ __device__ __forceinline__ uint64_t aligned_start(uint64_t s, uint32_t shift) {
 
 // ------------------------------------------------------------------ queue push
 // Warp-aggregated append: the lanes that push at the same time share one
-// atomicAdd on the counter.
-__device__ __forceinline__ void push(uint32_t* q, uint32_t* count, uint32_t v) {
+// atomicAdd on the counter.  A slot at or past `cap` is not written (the
+// count still records it, which the host reports).
+__device__ __forceinline__ void push(uint32_t* q, uint32_t* count, uint32_t cap, uint32_t v) {
     const unsigned mask = __activemask();
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(mask) - 1;
@@ -164,7 +167,7 @@ __device__ __forceinline__ void push(uint32_t* q, uint32_t* count, uint32_t v) {
     uint32_t base = 0;
     if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
     base = __shfl_sync(mask, base, leader);
-    q[base + rank] = v;
+    if ((uint64_t)base + rank < cap) q[base + rank] = v;
 }
 
 // Append a long list to the split-list queue: one 64-bit atomic hands out both
@@ -661,29 +664,31 @@ struct WarpQ {
     uint32_t cnt;   // entries held (the same in every lane)
 };
 
-// Appends the held entries (whole warp, converged).
-__device__ __forceinline__ void warpq_flush(WarpQ& wq, uint32_t* q, uint32_t* count) {
+// Appends the held entries (whole warp, converged).  Slots at or past `cap`
+// are not written; the count still records them, which the host reports.
+__device__ __forceinline__ void warpq_flush(WarpQ& wq, uint32_t* q, uint32_t* count, uint32_t cap) {
     if (wq.cnt == 0) return;
     const int lane = threadIdx.x & 31;
     uint32_t base = 0;
     if (lane == 0) base = atomicAdd(count, wq.cnt);
     base = __shfl_sync(0xffffffffu, base, 0);
     __syncwarp();
-    for (uint32_t i = lane; i < wq.cnt; i += 32) q[base + i] = wq.buf[i];
+    for (uint32_t i = lane; i < wq.cnt; i += 32)
+        if ((uint64_t)base + i < cap) q[base + i] = wq.buf[i];
     __syncwarp();
     wq.cnt = 0;
 }
 
 // Stages up to four ids per lane (whole warp, converged); the slots come from
 // ballot prefix counts.
-__device__ __forceinline__ void warpq_push4(WarpQ& wq, uint32_t* q, uint32_t* count, bool p0, bool p1, bool p2,
-                                            bool p3, uint4 id) {
+__device__ __forceinline__ void warpq_push4(WarpQ& wq, uint32_t* q, uint32_t* count, uint32_t cap, bool p0, bool p1,
+                                            bool p2, bool p3, uint4 id) {
     const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
     const unsigned b2 = __ballot_sync(0xffffffffu, p2), b3 = __ballot_sync(0xffffffffu, p3);
     const uint32_t n0 = __popc(b0), n1 = __popc(b1), n2 = __popc(b2);
     const uint32_t total = n0 + n1 + n2 + __popc(b3);
     if (total == 0) return;
-    if (wq.cnt + total > (uint32_t)kWarpBuf) warpq_flush(wq, q, count);
+    if (wq.cnt + total > (uint32_t)kWarpBuf) warpq_flush(wq, q, count, cap);
     const unsigned below = (1u << (threadIdx.x & 31)) - 1u;
     uint32_t* b = wq.buf + wq.cnt;
     if (p0) b[__popc(b0 & below)] = id.x;
@@ -712,7 +717,7 @@ __device__ __forceinline__ void visit_step(const Sweep& c, Op& op, typename Op::
         p1 = (p.valid & 2u) && op.visit(st, v, p.id.y, p.w.y, cur.y);
     }
     if (Op::kPush)
-        warpq_push4(wq, c.out_q, c.out_count, p0, p1, false, false,
+        warpq_push4(wq, c.out_q, c.out_count, c.qcap, p0, p1, false, false,
                     make_uint4((uint32_t)p.id.x, (uint32_t)p.id.y, 0u, 0u));
 }
 template <class Op>
@@ -734,7 +739,7 @@ __device__ __forceinline__ void visit_step(const Sweep& c, Op& op, typename Op::
         p2 = (p.valid & 4u) && op.visit(st, v, p.id.z, p.w.z, cur.z);
         p3 = (p.valid & 8u) && op.visit(st, v, p.id.w, p.w.w, cur.w);
     }
-    if (Op::kPush) warpq_push4(wq, c.out_q, c.out_count, p0, p1, p2, p3, p.id);
+    if (Op::kPush) warpq_push4(wq, c.out_q, c.out_count, c.qcap, p0, p1, p2, p3, p.id);
 }
 
 // Shared-memory staging buffers of the (at most 8) warps of a 256-thread block.
@@ -814,7 +819,7 @@ __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
             for (int u = 0; u < KS; u++) visit_step(c, op, st, v, p[u], cur[u], wq);
         }
     }
-    if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count);
+    if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count, c.qcap);
     add_scanned(c, scanned);
     op.flush();
 }
@@ -884,7 +889,7 @@ __global__ void __launch_bounds__(256) k_expand_all(Sweep c, Op op_in) {
             }
         }
     }
-    if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count);
+    if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count, c.qcap);
     add_scanned(c, scanned);
     op.flush();
 }
@@ -928,7 +933,7 @@ __device__ __forceinline__ void expand_split_body(const Sweep& c, Op& op) {
             for (int u = 0; u < KS; u++) visit_step(c, op, st, v, p[u], cur[u], wq);
         }
     }
-    if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count);
+    if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count, c.qcap);
     op.flush();
 }
 
@@ -990,7 +995,8 @@ __global__ void __launch_bounds__(256) k_bfs_bottom_up(Sweep c, uint32_t* level,
             uint32_t pos = 0;
             if (lane == 0) pos = atomicAdd(c.out_count, (uint32_t)__popc(fb));
             pos = __shfl_sync(0xffffffffu, pos, 0);
-            if (found) c.out_q[pos + __popc(fb & ((1u << lane) - 1u))] = (uint32_t)v;
+            const uint64_t slot = (uint64_t)pos + __popc(fb & ((1u << lane) - 1u));
+            if (found && slot < c.qcap) c.out_q[slot] = (uint32_t)v;
         }
         // lists still undecided: GPW of them at a time, G lanes each, read in
         // aligned 16-byte steps until the first neighbour on level L
@@ -1037,7 +1043,7 @@ __global__ void __launch_bounds__(256) k_bfs_bottom_up(Sweep c, uint32_t* level,
             if (mine && gfound && glane == 0) {
                 level[vv] = L + 1;
                 lf += ee - s0;
-                push(c.out_q, c.out_count, (uint32_t)vv);
+                push(c.out_q, c.out_count, c.qcap, (uint32_t)vv);
             }
         }
     }
@@ -1067,7 +1073,7 @@ __global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op_in) {
             const uint32_t u = ld_id<Id>(c.cols, i);
             const uint32_t w = Op::kWeights ? ld_w(c.w + i) : 0u;
             if (op.visit(st, v, u, w, Op::kPeek ? op.peek(u) : 0u) && Op::kPush)
-                push(c.out_q, c.out_count, (uint32_t)u);
+                push(c.out_q, c.out_count, c.qcap, (uint32_t)u);
         }
     }
     __syncwarp();
@@ -1093,7 +1099,7 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
             const uint32_t u = ld_id<Id>(c.cols, i);
             const uint32_t w = Op::kWeights ? ld_w(c.w + i) : 0u;
             if (op.visit(st, v, u, w, Op::kPeek ? op.peek(u) : 0u) && Op::kPush)
-                push(c.out_q, c.out_count, (uint32_t)u);
+                push(c.out_q, c.out_count, c.qcap, (uint32_t)u);
         }
     }
     __syncwarp();
@@ -1118,7 +1124,8 @@ __device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
     return ((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u);
 }
 
-__device__ __forceinline__ void compact_flags_body(uint8_t* flags, uint64_t nchunks, uint32_t* q, uint32_t* count) {
+__device__ __forceinline__ void compact_flags_body(uint8_t* flags, uint64_t nchunks, uint32_t* q, uint32_t* count,
+                                                   uint32_t cap) {
     __shared__ uint32_t warp_off[32];
     __shared__ uint32_t block_base;
     uint4* chunks = reinterpret_cast<uint4*>(flags);
@@ -1154,15 +1161,16 @@ __device__ __forceinline__ void compact_flags_body(uint8_t* flags, uint64_t nchu
         while (mask) {
             const uint32_t b = (uint32_t)__ffs((int)mask) - 1u;
             mask &= mask - 1u;
-            q[pos++] = (uint32_t)(ci * 16u + b);
+            if (pos < cap) q[pos] = (uint32_t)(ci * 16u + b);
+            pos++;
         }
         __syncthreads();  // warp_off and block_base are rewritten by the next pass
     }
 }
 
 static __global__ void __launch_bounds__(256) k_compact_flags(uint8_t* flags, uint64_t nchunks, uint32_t* q,
-                                                              uint32_t* count) {
-    compact_flags_body(flags, nchunks, q, count);
+                                                              uint32_t* count, uint32_t cap) {
+    compact_flags_body(flags, nchunks, q, count, cap);
 }
 
 // Block-aggregated queue append for kernels whose blocks step through the
@@ -1177,13 +1185,15 @@ struct BlockQueue {
     uint32_t base;
 };
 
-// Appends the buffered ids (whole block, converged).
-__device__ __forceinline__ void block_queue_flush(BlockQueue& bq, uint32_t* q, uint32_t* qcount) {
+// Appends the buffered ids (whole block, converged).  Slots at or past `cap`
+// are not written; the count still records them, which the host reports.
+__device__ __forceinline__ void block_queue_flush(BlockQueue& bq, uint32_t* q, uint32_t* qcount, uint32_t cap) {
     __syncthreads();
     const uint32_t k = bq.count;
     if (threadIdx.x == 0 && k) bq.base = atomicAdd(qcount, k);
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x) q[bq.base + i] = bq.ids[i];
+    for (uint32_t i = threadIdx.x; i < k; i += blockDim.x)
+        if ((uint64_t)bq.base + i < cap) q[bq.base + i] = bq.ids[i];
     __syncthreads();
     if (threadIdx.x == 0) bq.count = 0;
     __syncthreads();
@@ -1191,8 +1201,8 @@ __device__ __forceinline__ void block_queue_flush(BlockQueue& bq, uint32_t* q, u
 
 // Adds this thread's id if `p` (whole block, converged); flushes first when
 // one more pass of the block might not fit.
-__device__ __forceinline__ void block_queue_push(BlockQueue& bq, uint32_t* q, uint32_t* qcount, bool p,
-                                                 uint32_t id) {
+__device__ __forceinline__ void block_queue_push(BlockQueue& bq, uint32_t* q, uint32_t* qcount, uint32_t cap,
+                                                 bool p, uint32_t id) {
     const unsigned b = __ballot_sync(0xffffffffu, p);
     const int lane = threadIdx.x & 31;
     uint32_t slot = 0;
@@ -1202,7 +1212,7 @@ __device__ __forceinline__ void block_queue_push(BlockQueue& bq, uint32_t* q, ui
     __syncthreads();
     const uint32_t cnt = bq.count;
     __syncthreads();  // every thread has read the count before the next pass adds to it
-    if (cnt + blockDim.x > (uint32_t)kBlockBuf) block_queue_flush(bq, q, qcount);
+    if (cnt + blockDim.x > (uint32_t)kBlockBuf) block_queue_flush(bq, q, qcount, cap);
 }
 
 __device__ __forceinline__ void far_split_body(uint32_t n, uint32_t* fflag, const uint32_t* dist, const uint32_t* xd,
@@ -1218,8 +1228,12 @@ __device__ __forceinline__ void far_split_body(uint32_t n, uint32_t* fflag, cons
         bool near = false;
         if (v < n && fflag[v]) {
             const uint32_t d = dist[v];
-            if (d >= xd[v]) {
-                fflag[v] = 0u;  // already expanded with this distance
+            if (d >= xd[v] || qround[v] == round) {
+                // already expanded with this distance, or already in the queue:
+                // a vertex improved first to a far and then to a near distance
+                // in the last sweep is flagged and queued for sweep `round`
+                // (the window's tail, which this split appends behind)
+                fflag[v] = 0u;
             } else if (d < T) {
                 fflag[v] = 0u;
                 qround[v] = round;  // queued for the next sweep
@@ -1229,9 +1243,9 @@ __device__ __forceinline__ void far_split_body(uint32_t n, uint32_t* fflag, cons
                 lkept++;
             }
         }
-        block_queue_push(bq, nq_out, ncount_out, near, (uint32_t)v);
+        block_queue_push(bq, nq_out, ncount_out, n, near, (uint32_t)v);
     }
-    block_queue_flush(bq, nq_out, ncount_out);
+    block_queue_flush(bq, nq_out, ncount_out, n);
     warp_atomic_min(far_min, lmin);
     const uint32_t wk = __reduce_add_sync(0xffffffffu, lkept);
     if ((threadIdx.x & 31) == 0 && wk) atomicAdd(kept, wk);
@@ -1260,13 +1274,14 @@ struct SsspLoop {
     uint32_t sweeps;      // sweeps run (sweep stamp of the next sweep)
     uint32_t iters;       // sweeps + splits run
     uint32_t delta;       // window width
-    uint32_t error;       // 1 = the iteration cap was reached, 2 = the time bound
+    uint32_t error;       // 1 = the iteration cap was reached, 2 = the time bound, 3 = a queue count above n
     unsigned long long cap;
     unsigned long long t0, timeout_ns;  // %globaltimer at the first iteration; bound on the loop
     uint32_t* dist;       // this call's distance array
     uint32_t Th;          // long lists wait while their distance is at or above this
     uint32_t delta_heavy; // width of the long lists' part of a window
     unsigned long long tail;  // a sweep leaving fewer near vertices than this splits the far pile at once
+    uint32_t qcap;        // entries each frontier queue holds (n)
 };
 
 // The long lists' threshold of a window that starts at `lo`.
@@ -1323,7 +1338,7 @@ template <class Ctr>
 __global__ void __launch_bounds__(256) k_sssp_loop_compact(SsspFixed f, const SsspLoop* Lp, Ctr* ctr) {
     const SsspLoop L = *Lp;
     if (L.mode != 0) return;
-    compact_flags_body(f.nflag, f.nchunks, f.q[L.side ^ 1], &ctr->qcount[L.side ^ 1]);
+    compact_flags_body(f.nflag, f.nchunks, f.q[L.side ^ 1], &ctr->qcount[L.side ^ 1], f.base.qcap);
 }
 
 template <class Ctr>
@@ -1358,7 +1373,13 @@ __global__ void k_sssp_loop_control(SsspLoop* Lp, Ctr* ctr, cudaGraphConditional
     unsigned long long now;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(now));
     if (L.t0 == 0) L.t0 = now;
-    if (L.iters > L.cap) {
+    if (ctr->qcount[0] > L.qcap || ctr->qcount[1] > L.qcap) {
+        // appends past a queue's n entries were dropped: stop before a sweep
+        // reads the queue (this cannot happen while every vertex is queued at
+        // most once per sweep; the check makes a broken invariant an error)
+        L.error = 3;
+        L.mode = 2;
+    } else if (L.iters > L.cap) {
         L.error = 1;
         L.mode = 2;
     } else if (now - L.t0 > L.timeout_ns) {

@@ -84,6 +84,13 @@ extern "C" emogi_status emogi_bfs_noalloc(uint64_t n, const uint64_t* row_offset
         return (int)(b < 1 ? 1 : (b > (uint64_t)cap ? (uint64_t)cap : b));
     };
 
+    // The edge count (row_offsets[n]) lets a list's last ids come in one
+    // whole 16-byte load wherever that load ends inside the edge list, as in
+    // emogi_bfs; read into a host variable, which allocates nothing.
+    uint64_t m = 0;
+    EMOGI_CUDA_TRY(cudaMemcpyAsync(&m, row_offsets + n, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    EMOGI_CUDA_TRY(cudaStreamSynchronize(st));
+
     // the array keeps the previous call's contents: clear the counters
     EMOGI_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(DevCounters), st));
     dev::k_init_single<<<grid(n), threads, 0, st>>>(level, (uint32_t)n, (uint32_t)src, q0, nullptr,
@@ -112,11 +119,15 @@ extern "C" emogi_status emogi_bfs_noalloc(uint64_t n, const uint64_t* row_offset
         s.large_lines = 0xFFFFFFFFu;
         s.chunk_lines = 1;
         s.scanned = &ctr->scanned;
+        s.m = m;
+        s.qcap = (uint32_t)n;
         dev::k_expand_group<dev::BfsOp, 8><<<grid(k * 8), threads, 0, st>>>(s, dev::BfsOp{level, it + 1});
         EMOGI_CUDA_TRY(cudaGetLastError());
         uint32_t next = 0;
         EMOGI_CUDA_TRY(cudaMemcpyAsync(&next, &ctr->qcount[side ^ 1], sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         EMOGI_CUDA_TRY(cudaStreamSynchronize(st));
+        if (next > n) return fail(EMOGI_E_CUDA, "internal error: a BFS frontier of %u entries exceeds n = %llu",
+                                  next, (unsigned long long)n);
         k = next;
         side ^= 1;
     }

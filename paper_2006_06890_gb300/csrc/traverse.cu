@@ -128,6 +128,7 @@ Sweep make_sweep(const Ctx& c, int side, bool all_vertices) {
     s.scanned = &ws.ctr->scanned;
     s.heads = g->d_heads;
     s.m = g->m;
+    s.qcap = (uint32_t)g->n;
     return s;
 }
 
@@ -213,7 +214,7 @@ emogi_status compact_next(Ctx& c, int side) {
     Workspace& ws = c.g->ws;
     const uint64_t chunks = c.g->n / 16 + 1;
     dev::k_compact_flags<<<grid_for(c, chunks), kThreads, 0, c.st>>>(ws.nflag, chunks, ws.q[side],
-                                                                     &ws.ctr->qcount[side]);
+                                                                     &ws.ctr->qcount[side], (uint32_t)c.g->n);
     EMOGI_CUDA_TRY(cudaGetLastError());
     c.kernel_launches++;
     return EMOGI_OK;
@@ -267,6 +268,12 @@ emogi_status read_counters(Ctx& c, bool after_sweep = true) {
     Workspace& ws = c.g->ws;
     EMOGI_CUDA_TRY(cudaMemcpyAsync(ws.h_ctr, ws.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c.st));
     EMOGI_CUDA_TRY(cudaStreamSynchronize(c.st));
+    // a queue holds n entries and every append past them was dropped: a count
+    // above n is a broken invariant, reported before the queue is read again
+    for (int i = 0; i < 2; i++)
+        if (ws.h_ctr->qcount[i] > c.g->n)
+            return fail(EMOGI_E_CUDA, "internal error: frontier queue %d holds %u entries for n = %llu", i,
+                        ws.h_ctr->qcount[i], (unsigned long long)c.g->n);
     if (after_sweep && (c.o.flags & EMOGI_OPT_TIME_KERNELS)) {
         float ms = 0.f;
         EMOGI_CUDA_TRY(cudaEventElapsedTime(&ms, ws.ev[2], ws.ev[3]));
@@ -573,6 +580,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         hl->delta_heavy = (uint32_t)std::max<uint64_t>(std::min<uint64_t>(delta, dev::INF) / 8, 1);
         hl->Th = dev::heavy_threshold(0, hl->delta_heavy, hl->T);
         hl->tail = sssp_tail(g);
+        hl->qcap = (uint32_t)n;
         // the loop runs on the device: bound it in time as well (the caller's
         // timeout_ns when given, else one minute)
         hl->timeout_ns = (opts && opts->timeout_ns) ? opts->timeout_ns : 60000000000ull;
@@ -584,6 +592,9 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         EMOGI_CUDA_TRY(cudaMemcpyAsync(hl, ws.sssp_loop, sizeof *hl, cudaMemcpyDeviceToHost, c.st));
         EMOGI_TRY(read_counters(c));
         if (hl->error == 1) return fail(EMOGI_E_TIMEOUT, "SSSP did not converge in %u rounds", hl->iters);
+        if (hl->error == 3)
+            return fail(EMOGI_E_CUDA, "internal error: an SSSP frontier queue passed n = %llu entries after %u rounds",
+                        (unsigned long long)n, hl->iters);
         if (hl->error)
             return fail(EMOGI_E_TIMEOUT, "SSSP loop passed its time bound of %llu ns after %u rounds",
                         (unsigned long long)hl->timeout_ns, hl->iters);

@@ -233,6 +233,41 @@ def test_sssp_ordered_frontier(name):
             np.testing.assert_array_equal(E.sssp(h, s)[0], exp)  # and back to the queue form
 
 
+def far_then_near_multigraph(n, light):
+    """Source 0 has a heavy edge (255) and then a light one (`light`) to every
+    other vertex, plus a directed ring of weight 5 over vertices 1..n-1.  In
+    the first sweep each neighbour is improved first to a far distance (it is
+    flagged for the far pile) and then to a near one (it is queued), so the
+    window's tail and the far pile hold the same vertices."""
+    others = np.arange(1, n, dtype=np.uint64)
+    s = np.concatenate([np.zeros(2 * (n - 1), dtype=np.uint64), others])
+    d = np.concatenate([np.repeat(others, 2), np.concatenate([others[1:], others[:1]])])
+    w = np.concatenate([np.tile(np.array([255, light], dtype=np.uint32), n - 1),
+                        np.full(n - 1, 5, dtype=np.uint32)])
+    g = gg.csr_from_edges(n, s, d, weights=w, symmetrize=False, dedup=False, drop_self_loops=False,
+                          sort=False, name=f"far-then-near-{n}")
+    g.undirected = False
+    return g
+
+
+@pytest.mark.parametrize("n", [200, 256, 3000])
+@pytest.mark.parametrize("light,delta", [(0, 1), (1, 2), (1, 0)], ids=["w0-d1", "w1-d2", "w1-auto"])
+def test_sssp_vertex_both_far_and_near_in_one_sweep(n, light, delta):
+    """A vertex sent to the far pile and then queued near in the same sweep is
+    queued once: the far split that follows a kept window tail must not append
+    it behind the tail a second time (each queue holds n entries).  Host loop,
+    device loop and ordered frontiers, from device and host memory."""
+    g = far_then_near_multigraph(n, light)
+    exp = oracle.sssp_g(g, 0)
+    for placement in ("device", "host"):
+        with E.load_graph(g, placement=placement) as h:
+            for kw in (dict(), dict(host_loop=True), dict(ordered_frontier=True),
+                       dict(ordered_frontier=True, host_loop=True), dict(granularity=32)):
+                d, st = E.sssp(h, 0, delta=delta, **kw)
+                np.testing.assert_array_equal(d, exp, err_msg=f"{placement} {kw}")
+                assert st["edges_scanned"] <= 4 * g.m, (placement, kw, st)
+
+
 def test_sssp_device_loop_time_bound():
     """The device loop checks %globaltimer at every iteration; a 1 ns bound
     stops it with EMOGI_E_TIMEOUT, and the next call is exact again."""

@@ -5,7 +5,8 @@ heap, latency-critical loops that must not block or fail on allocation, or
 code sharing a context whose allocator it may not use) hand the library their
 own graph and output buffers; the library keeps its frontier queues in one
 fixed array per device instead of calling cudaMalloc.  This file checks,
-through the C ABI, that two calls in a row give exactly what emogi_bfs gives.
+through the C ABI, that two calls in a row give exactly what emogi_bfs and
+the oracle's BFS give, at the largest size the array allows too.
 It is collected after the other parity tests (only the full-size cases come
 later) so that a failure here hides none of them.
 """
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +55,34 @@ def test_two_calls_in_a_row_match_emogi_bfs(edges_in):
             got = level.cpu().numpy().view(np.uint32)
             want, _ = E.bfs(h, src)
             np.testing.assert_array_equal(got, want)
+            np.testing.assert_array_equal(got, oracle.bfs_g(g, src))
     assert E.device_bytes_in_use() == in_use
+
+
+def test_maximum_size_and_unaligned_edge_list():
+    """n at the maximum the fixed array is sized for, on a uniform graph with
+    device edges, then the same edge list seen through
+    a view 16 bytes past a 128-byte boundary (list reads start at another
+    offset within their line)."""
+    n = E.NOALLOC_MAX_VERTICES
+    g = gg.uniform(n, 8, seed=11)
+    off, cols = _device_csr(g)
+    padded = torch.zeros(g.m + 16, dtype=torch.int64, device="cuda")
+    assert padded.data_ptr() % 128 == 0
+    shifted = padded[2:2 + g.m]
+    shifted.copy_(cols)
+    assert shifted.data_ptr() % 128 == 16
+    level = torch.empty(n, dtype=torch.int32, device="cuda")
+    srcs = [gg.max_degree_vertex(g), int(gg.random_sources(g, 1, seed=3)[0])]
+    with E.load_graph(g, placement="device") as h:
+        for src in srcs:
+            want = oracle.bfs_g(g, src)
+            np.testing.assert_array_equal(E.bfs(h, src)[0], want)
+            for c in (cols, shifted):
+                level.fill_(-7)
+                E.bfs_noalloc(n, off, c, src, level)
+                torch.cuda.synchronize()
+                np.testing.assert_array_equal(level.cpu().numpy().view(np.uint32), want)
 
 
 def test_sizes_beyond_the_maximum_are_rejected():
