@@ -26,6 +26,8 @@ _lib_handle = None
 
 KRON = 0
 UNIFORM = 1
+# vertex blocks of the final sort-and-pack pass (the result does not depend on it)
+FINISH_BLOCKS = 4096
 
 
 def build_lib(force: bool = False) -> str:
@@ -45,11 +47,11 @@ def _lib():
         p = ctypes.c_void_p
         lib.gg_rand.restype = u64
         lib.gg_rand.argtypes = [u64, u64]
-        lib.gg_perm.argtypes = [u64, u64, p]
-        lib.gg_sample.argtypes = [i32, u64, i32, u64, p, u64, u64, p, p]
-        lib.gg_count.argtypes = [i32, u64, i32, u64, p, u64, p]
-        lib.gg_fill.argtypes = [i32, u64, i32, u64, p, u64, p, p, p, p]
-        lib.gg_compact.argtypes = [u64, p, p, p, p]
+        lib.gg_relabel_table.argtypes = [i32, u64, p]
+        lib.gg_sample.argtypes = [i32, u64, i32, u64, i32, u64, u64, p, p]
+        lib.gg_count.argtypes = [i32, u64, i32, u64, i32, u64, i32, p, p]
+        lib.gg_fill.argtypes = [i32, u64, i32, u64, i32, u64, i32, p, p, p]
+        lib.gg_finish.argtypes = [u64, p, p, u64, p, p, p]
         lib.gg_weights.argtypes = [u64, p, p, u64, p]
         lib.gg_num_threads.restype = i32
         _lib_handle = lib
@@ -91,6 +93,28 @@ def aligned_empty(count: int, dtype, align: int = 4096) -> np.ndarray:
     return raw[off:off + nbytes].view(dtype)[:int(count)]
 
 
+def release_host_range(arr: np.ndarray, lo: int, hi: int) -> int:
+    """Return the physical pages wholly inside elements [lo, hi) of a 1-D
+    array to the operating system (madvise MADV_DONTNEED; for anonymous
+    memory those pages then read as zeros).  Lets a caller that has copied
+    a large array elsewhere in pieces free each piece at once, so that the
+    two copies never coexist.  Returns the bytes released."""
+    item = arr.dtype.itemsize
+    a = arr.ctypes.data + max(0, int(lo)) * item
+    b = arr.ctypes.data + min(int(hi), arr.size) * item
+    page = mmap.PAGESIZE
+    a = (a + page - 1) // page * page
+    b = b // page * page
+    if b <= a:
+        return 0
+    libc = ctypes.CDLL(None, use_errno=True)
+    libc.madvise.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+    MADV_DONTNEED = 4
+    if libc.madvise(ctypes.c_void_p(a), ctypes.c_size_t(b - a), MADV_DONTNEED) != 0:
+        raise OSError(ctypes.get_errno(), "madvise(MADV_DONTNEED) failed")
+    return b - a
+
+
 @dataclass
 class Graph:
     """A CSR graph: offsets uint64[n+1], cols uint64[m], optional weights uint32[m]."""
@@ -114,38 +138,46 @@ def rand(seed: int, i: int) -> int:
     return int(_lib().gg_rand(seed & (2**64 - 1), i))
 
 
-def permutation(n: int, seed: int) -> np.ndarray:
-    perm = np.empty(n, dtype=np.uint64)
-    _lib().gg_perm(n, seed, _ptr(perm))
+def relabelling(scale: int, seed: int) -> np.ndarray:
+    """The seeded bijection of [0, 2^scale) that relabels Kronecker vertex ids
+    (entry x = the new id of x)."""
+    perm = np.empty(1 << scale, dtype=np.uint64)
+    _lib().gg_relabel_table(scale, seed, _ptr(perm))
     return perm
 
 
 def samples(kind: int, n: int, scale: int, seed: int, count: int, permute: bool = True,
             k0: int = 0):
     """Raw edge samples (before cleaning) of a generated graph."""
-    perm = permutation(n, seed) if (kind == KRON and permute) else None
     src = np.empty(count, dtype=np.uint64)
     dst = np.empty(count, dtype=np.uint64)
-    _lib().gg_sample(kind, n, scale, seed, _ptr(perm), k0, count, _ptr(src), _ptr(dst))
+    _lib().gg_sample(kind, n, scale, seed, int(bool(permute)), k0, count, _ptr(src), _ptr(dst))
     return src, dst
 
 
 def _build(kind: int, n: int, scale: int, nsamples: int, seed: int, permute: bool,
            with_weights: bool, wseed: int, name: str) -> Graph:
     lib = _lib()
-    perm = permutation(n, seed) if (kind == KRON and permute) else None
-    deg = np.zeros(n, dtype=np.uint64)
-    lib.gg_count(kind, n, scale, seed, _ptr(perm), nsamples, _ptr(deg))
-    off_raw = np.zeros(n + 1, dtype=np.uint64)
+    pm = int(bool(permute and kind == KRON))
+    deg = aligned_empty(n, np.uint64)
+    # per-part vertex counts (no atomics in either pass); more parts than
+    # threads would only cost memory, fewer would idle threads.  The arrays
+    # that both passes update at random sit on huge pages (aligned_empty) so
+    # that those updates rarely miss the TLB.
+    parts = max(1, min(num_threads(), 64, max(1, nsamples // 4096)))
+    cnt = aligned_empty(parts * n, np.uint32)
+    lib.gg_count(kind, n, scale, seed, pm, nsamples, parts, _ptr(cnt), _ptr(deg))
+    off_raw = aligned_empty(n + 1, np.uint64)
+    off_raw[0] = 0
     np.cumsum(deg, out=off_raw[1:])
     m_raw = int(off_raw[-1])
     cols = aligned_empty(m_raw, np.uint64)
-    cursor = np.empty(n, dtype=np.uint64)
-    lib.gg_fill(kind, n, scale, seed, _ptr(perm), nsamples, _ptr(off_raw), _ptr(cursor),
-                _ptr(cols), _ptr(deg))
-    del cursor
+    lib.gg_fill(kind, n, scale, seed, pm, nsamples, parts, _ptr(cnt), _ptr(off_raw), _ptr(cols))
+    del cnt
     off = np.empty(n + 1, dtype=np.uint64)
-    lib.gg_compact(n, _ptr(off_raw), _ptr(deg), _ptr(cols), _ptr(off))
+    nblocks = max(1, min(n, FINISH_BLOCKS))
+    blk = np.empty(nblocks, dtype=np.uint64)
+    lib.gg_finish(n, _ptr(off_raw), _ptr(cols), nblocks, _ptr(blk), _ptr(deg), _ptr(off))
     m = int(off[-1])
     cols = cols[:m]
     w = None
@@ -273,10 +305,10 @@ def max_degree_vertex(g: Graph) -> int:
     return int(np.argmax(g.degrees())) if g.n else 0
 
 
-def random_sources(g: Graph, count: int, seed: int = 2, min_degree: int = 1) -> np.ndarray:
-    """`count` distinct seeded vertices with out-degree >= min_degree."""
-    deg = g.degrees()
-    cand = np.nonzero(deg >= min_degree)[0]
+def pick_seeded(candidates, count: int, seed: int) -> np.ndarray:
+    """`count` distinct entries of `candidates` drawn by the seeded stream
+    (value i of the stream picks candidate floor(r_i * size / 2^64))."""
+    cand = np.asarray(candidates)
     if cand.size == 0:
         return np.zeros(0, dtype=np.uint64)
     out, seen, i = [], set(), 0
@@ -287,6 +319,11 @@ def random_sources(g: Graph, count: int, seed: int = 2, min_degree: int = 1) -> 
             seen.add(j)
             out.append(j)
     return np.array(out, dtype=np.uint64)
+
+
+def random_sources(g: Graph, count: int, seed: int = 2, min_degree: int = 1) -> np.ndarray:
+    """`count` distinct seeded vertices with out-degree >= min_degree."""
+    return pick_seeded(np.nonzero(g.degrees() >= min_degree)[0], count, seed)
 
 
 def num_threads() -> int:

@@ -61,9 +61,12 @@ def test_generation_is_deterministic_across_thread_counts():
     assert outs[0] == outs[1]
 
 
-def test_seeds_differ_and_permutation_is_bijective():
-    p = gg.permutation(1000, 5)
-    assert np.array_equal(np.sort(p), np.arange(1000, dtype=np.uint64))
+def test_seeds_differ_and_relabelling_is_bijective():
+    for scale in (1, 2, 7, 10, 16):
+        p = gg.relabelling(scale, 5)
+        assert np.array_equal(np.sort(p), np.arange(1 << scale, dtype=np.uint64))
+    p, q = gg.relabelling(12, 5), gg.relabelling(12, 6)
+    assert not np.array_equal(p, q) and not np.array_equal(p, np.arange(1 << 12, dtype=np.uint64))
     a = gg.kronecker(10, 8, seed=1)
     b = gg.kronecker(10, 8, seed=2)
     assert not np.array_equal(a.cols[:100], b.cols[:100])
@@ -88,3 +91,45 @@ def test_csr_from_edges_keeps_duplicates_when_asked():
 def test_aligned_allocation():
     a = gg.aligned_empty(1000, np.uint64, 4096)
     assert a.ctypes.data % 4096 == 0 and a.size == 1000
+
+
+def test_builder_equals_a_plain_csr_of_the_raw_samples(monkeypatch):
+    """The C builder (per-part counts, scatter, block sort-and-pack) gives the
+    CSR that numpy builds from the same raw samples: self-loops dropped, both
+    directions, rows sorted and de-duplicated; whatever the number of blocks
+    of the pack pass (a dense graph, so that later blocks move by more than
+    their own length and are copied in parallel chunks)."""
+    scale, ef = 12, 64
+    n = 1 << scale
+    src, dst = gg.samples(gg.KRON, n, scale, seed=4, count=ef * n)
+    ref = gg.csr_from_edges(n, src, dst)
+    assert ref.m < 0.6 * 2 * ef * n  # many duplicates
+    for blocks in (1, 2, 3, 4096):
+        monkeypatch.setattr(gg, "FINISH_BLOCKS", blocks)
+        g = gg.kronecker(scale, ef, seed=4)
+        assert np.array_equal(g.offsets, ref.offsets), blocks
+        assert np.array_equal(g.cols, ref.cols), blocks
+    u = gg.uniform(5000, 9, seed=3)
+    us, ud = gg.samples(gg.UNIFORM, 5000, 0, seed=3, count=int(round(5000 * 9 / 2)))
+    ur = gg.csr_from_edges(5000, us, ud)
+    assert np.array_equal(u.offsets, ur.offsets) and np.array_equal(u.cols, ur.cols)
+
+
+def test_kronecker_quadrant_frequencies():
+    """Each bit level of a raw (unrelabelled) sample picks quadrant
+    (0,0), (0,1), (1,0), (1,1) with probabilities 0.57, 0.19, 0.19, 0.05."""
+    scale = 10
+    src, dst = gg.samples(gg.KRON, 1 << scale, scale, seed=9, count=200_000, permute=False)
+    for lvl in (0, 3, 4, 9):
+        bu = (src >> np.uint64(lvl)) & np.uint64(1)
+        bv = (dst >> np.uint64(lvl)) & np.uint64(1)
+        f = [np.mean((bu == a) & (bv == b)) for a, b in ((0, 0), (0, 1), (1, 0), (1, 1))]
+        np.testing.assert_allclose(f, [0.57, 0.19, 0.19, 0.05], atol=0.005)
+
+
+def test_release_host_range_frees_pages_of_a_large_array():
+    a = gg.aligned_empty((1 << 30) // 8 + 1024, np.uint64)
+    a[:] = 7
+    released = gg.release_host_range(a, 1000, a.size - 1000)
+    assert released > (1 << 29)
+    assert a[0] == 7 and a[-1] == 7 and a[a.size // 2] == 0
