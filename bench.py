@@ -1,20 +1,27 @@
-"""Benchmark: BFS + SSSP + CC over an undirected uniform-random graph whose edge
-and weight arrays sit in pinned host memory and are read zero-copy.
+"""Benchmark: BFS + SSSP + CC over an undirected Kronecker graph of scale 27
+(edge factor 32) whose edge and weight arrays sit in pinned host memory and
+are read zero-copy, with the device held to a 16 GiB budget.
 
-Workload: 2^24 vertices, 2^28 uniform samples stored in both directions
-(about 5.4e8 directed uint64 edges = 4.3 GB, plus 2.1 GB of uint32 weights in
-[1, 255]); vertex state in GPU memory.  One step = BFS + SSSP from the same
-seeded source (16 sources, used in turn) + CC.
+Workload (the paper's scale, Sec. 5.2 and the 16 GB device of Sec. 5.6):
+2^27 vertices, 2^32 Kronecker samples stored in both directions and cleaned
+(about 8.6e9 directed uint64 edges = 69 GB, plus 34 GB of uint32 weights in
+[1, 255]), generated on huge pages and pinned in place (no copy); offsets,
+list heads and vertex state in HBM.  One step = BFS + SSSP from one of 16
+seeded sources of the giant component (used in turn) + CC.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload kron27|urand24]
 
 Prints one JSON line.  `value` is GTEPS over the whole step (edges out of
 reached vertices for BFS and SSSP, all m edges for CC, divided by the
-device-timed step), with the graph resident (edges in pinned host memory,
-offsets in HBM).  `e2e` repeats the step through the public API with host
-output buffers, so every step's D2H result copy (and the source ids sent to
-the device) sit inside the timed region.  `--impl reference` times the CPU
-oracle instead (the paper's method has no public implementation to run).
+device-timed step), with the graph resident.  `e2e` repeats the step through
+the public API with host output buffers, so every step's D2H result copy (and
+the source id sent to the device) sits inside the timed region.  Beside it:
+`variants.managed_capped` (the same graph in managed memory with 16 GiB of
+HBM left to the library and UVM), an uncapped managed point, and the uniform
+2^24 workload with its access-pattern and placement variants (`c2`).
+`--impl reference` times the CPU oracle instead (the paper's method has no
+public implementation to run).
 """
 from __future__ import annotations
 
@@ -33,10 +40,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "GTEPS and % of host-link/HBM peak for BFS/SSSP/CC; batched queries/s at p99"
-SCALE_N = 1 << 24
-AVG_DEGREE = 32
 GEN_SEED, SRC_SEED = 1, 2
 N_SOURCES = 16
+KRON27 = dict(scale=27, ef=32)
+DEVICE_BUDGET = 16 << 30  # the paper's 16 GB GPU (Sec. 5.6 throttles its A100 to 16 GB)
+URAND24 = dict(n=1 << 24, degree=32)
+SOURCES_FILE = os.path.join(ROOT, "tests", "golden", "kron27_ef32_sources.txt")
 
 
 def parse():
@@ -45,22 +54,23 @@ def parse():
     ap.add_argument("--steps", type=int, default=8)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=SCALE_N, help="vertices (power of two)")
-    ap.add_argument("--degree", type=int, default=AVG_DEGREE)
-    ap.add_argument("--no-variants", action="store_true", help="skip the naive/managed/device comparison")
+    ap.add_argument("--workload", default="kron27", choices=["kron27", "urand24"],
+                    help="kron27 = the default line (Kronecker scale 27, edge factor 32, edges and weights "
+                         "pinned in place in host memory, 16 GiB device budget); urand24 = uniform 2^24, "
+                         "degree 32 (the c2 workload) as the headline")
+    ap.add_argument("--no-variants", action="store_true", help="skip the managed / access-pattern comparisons")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="urand24", choices=["urand24", "kron27"],
-                    help="urand24 = the default bench line; kron27 = BFS, SSSP and CC from 4 seeded sources on an "
-                         "undirected Kronecker graph of scale 27, edge factor 32 (about 7e9 edges, 60+ GB edges "
-                         "and 30 GB weights) pinned in place in host memory, with a 16 GB device budget")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the multi-source, batched and serving measurements")
+                    help="skip the uniform 2^24 block and the multi-source, batched and serving measurements")
     ap.add_argument("--ncu-case", nargs="?", const="traversal", default=None,
-                    choices=["traversal", "msbfs", "batch", "pagerank"],
+                    choices=["traversal", "msbfs", "batch", "pagerank", "kron", "access"],
                     help="profiling case, then exit: 'traversal' = one BFS, SSSP and CC on a 2^22-vertex uniform "
-                         "graph (1.1 GB edges in pinned host memory); 'msbfs' = one 64-source pass on a scale-22 "
-                         "Kronecker graph in host memory; 'batch' = one batched BFS over 128 uneven graphs in HBM; "
-                         "'pagerank' = 3 PageRank iterations on the 2^22-vertex uniform graph in host memory")
+                         "graph (1.1 GB edges in pinned host memory); 'kron' = the same on a Kronecker graph of "
+                         "scale 23, edge factor 32 (2.2 GB edges in host memory); 'access' = top-down BFS on the "
+                         "2^22 uniform graph with the naive, merged and merged+aligned reads; 'msbfs' = one "
+                         "64-source pass on a scale-22 Kronecker graph in host memory; 'batch' = one batched BFS "
+                         "over 128 uneven graphs in HBM; 'pagerank' = 3 PageRank iterations on the 2^22 uniform "
+                         "graph in host memory")
     return ap.parse_args()
 
 
@@ -71,22 +81,62 @@ def dist_env():
     return rank, world, local
 
 
-def make_graph(n, degree):
+def read_kron27_sources():
+    """The stored sources of the scale-27 workload (written by the oracle's
+    union-find over the whole graph: tests/golden/make_kron27_sources.py)."""
+    info = {}
+    if not os.path.exists(SOURCES_FILE):
+        return info
+    for line in open(SOURCES_FILE):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, _, v = line.strip().partition(" ")
+        info[k] = [int(x) for x in v.split()] if k == "sources" else int(v)
+    return info
+
+
+def make_kron27():
+    """The scale-27 graph on huge pages and its 16 giant-component sources
+    (the stored list when it belongs to this graph, else 16 seeded vertices
+    of degree >= 2, and the config says so)."""
+    import graphgen as gg
+    t0 = time.perf_counter()
+    g = gg.kronecker(KRON27["scale"], KRON27["ef"], seed=GEN_SEED, weights=True)
+    gen_s = time.perf_counter() - t0
+    info = read_kron27_sources()
+    if info.get("n") == g.n and info.get("m") == g.m and len(info.get("sources", [])) == N_SOURCES:
+        srcs, how = info["sources"], "16 seeded vertices of the giant component (oracle union-find, stored)"
+    else:
+        srcs = [int(s) for s in gg.random_sources(g, N_SOURCES, seed=SRC_SEED, min_degree=2)]
+        how = "16 seeded vertices of degree >= 2 (no stored giant-component list for this graph)"
+    return g, srcs, {"generation_s": round(gen_s, 1), "sources_from": how}
+
+
+def make_urand24(n=URAND24["n"], degree=URAND24["degree"]):
     import graphgen as gg
     g = gg.uniform(n, degree, seed=GEN_SEED, weights=True)
     srcs = gg.random_sources(g, N_SOURCES, seed=SRC_SEED)
     return g, [int(s) for s in srcs]
 
 
-def workload_config(g, n, degree, extra=None):
-    cfg = {"workload": f"uniform-random n=2^{n.bit_length() - 1} avg-degree {degree}: BFS+SSSP+CC, "
-                       "edges+weights in pinned host memory (zero-copy), vertex state in HBM",
-           "n": g.n, "m": g.m, "edge_bytes": g.m * 8, "weight_bytes": g.m * 4,
-           "sources": N_SOURCES, "placement": "host", "access": "merged_aligned",
-           "l2": "inputs larger than L2 (4.3 GB edge list in host memory); no flush"}
-    if extra:
-        cfg.update(extra)
-    return cfg
+def workload_config(workload, m):
+    """The `config` of the bench line, the same for both arms (m = the graph's
+    directed edge count)."""
+    if workload == "kron27":
+        return {"workload": "Kronecker scale 27, edge factor 32 (initiator 0.57/0.19/0.19/0.05, ids relabelled, "
+                            "cleaned, symmetric): BFS+SSSP+CC, uint64 edges + uint32 weights pinned in place in "
+                            "host memory (zero-copy), vertex state in HBM, 16 GiB device budget",
+                "n": 1 << KRON27["scale"], "m": m, "edge_bytes": m * 8 if m else None,
+                "weight_bytes": m * 4 if m else None, "sources": N_SOURCES,
+                "placement": "host (borrowed, huge pages)", "device_budget_bytes": DEVICE_BUDGET,
+                "access": "merged_aligned", "step": "BFS + SSSP from one source, then CC",
+                "l2": "inputs larger than L2 (69 GB edge list in host memory); no flush"}
+    return {"workload": f"uniform-random n=2^24 avg-degree 32: BFS+SSSP+CC (the SSSP + CC workload with BFS "
+                        "added), edges+weights in pinned host memory (zero-copy), vertex state in HBM",
+            "n": URAND24["n"], "m": m, "edge_bytes": m * 8 if m else None, "weight_bytes": m * 4 if m else None,
+            "sources": N_SOURCES, "placement": "host", "access": "merged_aligned",
+            "step": "BFS + SSSP from one source, then CC",
+            "l2": "inputs larger than L2 (4.3 GB edge list in host memory); no flush"}
 
 
 # ------------------------------------------------------------------ clocks
@@ -197,28 +247,33 @@ def step_teps_edges(stats):
     return sb["edges_reached"] + ss["edges_reached"] + sc["edges_reached"]
 
 
+def link_bytes(st):
+    """Algorithmic bytes a call read from the edge list (and weights) in host
+    memory: 8 B per id (4 B with 4-byte ids) and 4 B per weight of the list
+    entries read there; entries of lists served from the short-list store in
+    GPU memory are not counted."""
+    return st["edge_bytes"] + st["weight_bytes"]
+
+
 def step_alg_bytes(stats):
-    """Algorithmic link bytes of the expansion launches: 8 B per list entry read
-    (BFS, CC) and 12 B per entry (SSSP: id + weight), over the entries the
-    launches actually process (direction-optimising BFS and sampled CC read
-    fewer entries than the reached edges; SSSP re-expands a few)."""
-    sb, ss, sc = stats
-    return 8 * sb["edges_scanned"] + 12 * ss["edges_scanned"] + 8 * sc["edges_scanned"]
+    """Algorithmic link bytes of one step's expansion launches (BFS, SSSP, CC)."""
+    return sum(link_bytes(s) for s in stats)
 
 
 # Host-link read bytes per algorithmic byte of the expansion kernels, from the
-# ncu sysmem read-sector counts of the same kernels on the 2^22-vertex case
-# (profiles/link_traffic_per_kernel_urand22_host.md); the 32-byte sector waste
-# of lists that do not start on a sector grows with the entries read, so the
-# per-entry factor scales to the 2^24 graph.
-LINK_BYTES_PER_ALG_BYTE = {"bfs": 1.130, "sssp": 1.135, "cc": 1.0}
+# ncu sysmem read-sector counts of the same kernels on a smaller graph of the
+# same family (uniform: 2^22 vertices, profiles/link_traffic_per_kernel_
+# urand22_host.md; Kronecker: scale 23, profiles/link_traffic_per_kernel_
+# kron23_host.md); the 32-byte sector waste of lists that do not start on a
+# sector grows with the entries read, so the per-entry factor scales to the
+# full graph.  None = not measured for the current kernels.
+LINK_BYTES_PER_ALG_BYTE = {"urand": {"bfs": 1.130, "sssp": 1.135, "cc": 1.0},
+                           "kron": None}
 
 
-def step_link_bytes(stats):
+def step_link_bytes(stats, factors):
     sb, ss, sc = stats
-    return (LINK_BYTES_PER_ALG_BYTE["bfs"] * 8 * sb["edges_scanned"] +
-            LINK_BYTES_PER_ALG_BYTE["sssp"] * 12 * ss["edges_scanned"] +
-            LINK_BYTES_PER_ALG_BYTE["cc"] * 8 * sc["edges_scanned"])
+    return factors["bfs"] * link_bytes(sb) + factors["sssp"] * link_bytes(ss) + factors["cc"] * link_bytes(sc)
 
 
 def combine_over_ranks(ms, units, world, device="cuda"):
@@ -255,10 +310,221 @@ def time_loop(torch, E, h, srcs, stream, steps, warmup, outs):
 VARIANT_STEPS = 4  # sources each comparison variant is timed on (after one untimed step)
 
 
+def per_algorithm(per):
+    out = {}
+    for i, nm in enumerate(("bfs", "sssp", "cc")):
+        e = sum(p[i]["edges_reached"] for p in per)
+        t = sum(p[i]["ms"] for p in per)
+        out[nm] = {"gteps": round(e / (t * 1e-3) / 1e9, 3), "ms_mean": round(t / len(per), 3),
+                   "iterations_mean": round(sum(p[i]["iterations"] for p in per) / len(per), 2),
+                   "edges_scanned_over_reached": round(sum(p[i]["edges_scanned"] for p in per) / max(e, 1), 3),
+                   "link_gbs_useful": round(sum(link_bytes(p[i]) for p in per) /
+                                            max(sum(p[i]["expand_ms"] for p in per), 1e-9) / 1e6, 1)}
+        sc = sum(p[i]["edges_scanned"] for p in per)
+        if sc and nm != "cc":
+            ids = sum(p[i]["edge_bytes"] for p in per) / 8  # the bench graphs have uint64 ids
+            out[nm]["entries_from_gpu_memory"] = round(1.0 - ids / sc, 4)
+    return out
+
+
+def roofline(per, link_peak, factors, peaks, kernel):
+    """Roofline of the dominant kernel, the recorded SSSP loop (one graph
+    launch per call: its sweeps, far splits and controller; SSSP is most of
+    the step): algorithmic bytes (12 B per list entry read: id + weight) over
+    the loop's device time, against the pinned host->device copy peak.  The
+    same fraction over every expansion launch of the step (BFS and CC read
+    8 B per list entry) is reported beside it."""
+    sssp_ms = sum(p[1]["expand_ms"] for p in per)
+    sssp_bytes = sum(link_bytes(p[1]) for p in per)
+    achieved = sssp_bytes / (sssp_ms * 1e-3) / 1e9
+    expand_ms = sum(s["expand_ms"] for p in per for s in p)
+    alg_bytes = sum(step_alg_bytes(p) for p in per)
+    r = {"bound": "host_link", "kernel": kernel, "achieved": round(achieved, 2), "peak": round(link_peak, 2),
+         "unit": "GB/s", "frac": round(achieved / link_peak, 4),
+         "peak_source": "pinned host->device cudaMemcpy, 1 GiB, best of 6, measured in this run",
+         "algorithmic_bytes_per_launch": int(sssp_bytes / len(per)),
+         "unit_bytes": "12 B per SSSP list entry read from host memory (8 B id + 4 B weight); entries of lists "
+                       "served by the short-list store in GPU memory are not counted",
+         "launch_ms": round(sssp_ms / len(per), 3),
+         "step_expansion": {"algorithmic_bytes": int(alg_bytes / len(per)), "ms": round(expand_ms / len(per), 3),
+                            "frac": round(alg_bytes / (expand_ms * 1e-3) / 1e9 / link_peak, 4),
+                            "note": "every expansion launch of the step: 8 B per BFS / CC list entry, 12 B per "
+                                    "SSSP entry"},
+         "hbm_peak_measured_gbs": peaks.get("hbm_gbs")}
+    if factors:
+        link = sum(factors["sssp"] * link_bytes(p[1]) for p in per)
+        r["traffic"] = int(link / len(per))
+        r["traffic_note"] = ("host-link read bytes per SSSP call: ncu sysmem read sectors x 32 per list entry on a "
+                             f"smaller graph of the same family ({factors['sssp']} per algorithmic byte), scaled "
+                             "by this run's entries")
+        r["link_frac"] = round(link / (sssp_ms * 1e-3) / 1e9 / link_peak, 4)
+    else:
+        r["traffic"] = None
+        r["traffic_note"] = "no sysmem sector count of the current kernels on this graph family yet"
+    return r
+
+
+KERNEL_NOTE = ("the recorded SSSP loop, timed as one graph launch per call: k_sssp_loop_sweep (merged + aligned "
+               "list reads), k_sssp_loop_lists (split lists), k_sssp_loop_compact, k_sssp_loop_far, "
+               "k_sssp_loop_control")
+
+
+def headline(torch, E, h, g, srcs, stream, args, world, barrier):
+    """The timed step loop (value) and the same step through the public API
+    with pinned host outputs (e2e)."""
+    outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(3)]
+    barrier()
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        ms, wall, per = time_loop(torch, E, h, srcs, stream, args.steps, args.warmup, outs)
+    barrier()
+    ms, teps_edges = combine_over_ranks(ms, sum(step_teps_edges(p) for p in per), world)
+    del outs
+    e2e_steps = max(2, args.steps // 4)
+    host_outs = [torch.empty(g.n, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32) for _ in range(3)]
+    barrier()
+    ms_e2e, _, per_e2e = time_loop(torch, E, h, srcs, stream, e2e_steps, 1, host_outs)
+    barrier()
+    ms_e2e, e2e_edges = combine_over_ranks(ms_e2e, sum(step_teps_edges(p) for p in per_e2e), world)
+    del host_outs
+    return {"ms": ms, "wall": wall, "per": per, "value": teps_edges / (ms * 1e-3) / 1e9, "clocks": clk.summary(),
+            "e2e": {"value": round(e2e_edges / (ms_e2e * 1e-3) / 1e9, 4), "unit": "GTEPS", "steps": e2e_steps,
+                    "h2d_bytes_per_step": 2 * 8, "d2h_bytes_per_step": 3 * 4 * g.n,
+                    "note": "public API with pinned host output arrays: each call copies its n-entry result to "
+                            "the host inside the timed region"}}
+
+
+def variant_steps(E, hv, srcs, stream, outs, okw, sssp_timeout_ns=0):
+    """One untimed step, then one timed step per source; returns the summary."""
+    def one(src):
+        sb = E.bfs(hv, src, stream=stream, out=outs[0], **okw)[1]
+        ss = E.sssp(hv, src, stream=stream, out=outs[1], timeout_ns=sssp_timeout_ns, **okw)[1]
+        sc = E.cc(hv, stream=stream, out=outs[2], **okw)[1]
+        return (sb, ss, sc)
+
+    t0 = time.perf_counter()
+    one(srcs[0])
+    cold_s = time.perf_counter() - t0
+    sts = [one(x) for x in srcs]
+    tot_ms = sum(s["ms"] for st in sts for s in st)
+    k = len(sts)
+    return {"gteps": round(sum(step_teps_edges(st) for st in sts) / (tot_ms * 1e-3) / 1e9, 4),
+            "ms_per_step": round(tot_ms / k, 3), "first_step_s": round(cold_s, 3), "steps": k,
+            "bfs_ms": round(sum(st[0]["ms"] for st in sts) / k, 3),
+            "sssp_ms": round(sum(st[1]["ms"] for st in sts) / k, 3),
+            "cc_ms": round(sum(st[2]["ms"] for st in sts) / k, 3)}
+
+
+def to_managed(E, gg, a, threads=8):
+    """A managed copy of a large host array, made piece by piece; each piece
+    of the host array is returned to the OS once copied, so the two copies
+    never coexist (the host holds one copy of a 100 GB graph, not two)."""
+    from concurrent.futures import ThreadPoolExecutor
+    mo = E.managed_empty(a.size, a.dtype)
+    piece = (256 << 20) // a.dtype.itemsize
+    group = piece * threads
+
+    def cp(i):
+        mo[i:i + piece] = a[i:i + piece]
+
+    with ThreadPoolExecutor(threads) as ex:
+        for base in range(0, a.size, group):
+            list(ex.map(cp, range(base, min(base + group, a.size), piece)))
+            gg.release_host_range(a, base, base + group)
+    return mo
+
+
+MANAGED_SSSP_BOUND_S = 60  # time bound on one capped-UVM SSSP (the zero-copy SSSP takes under 2 s)
+
+
+def managed_step(E, hm, src, stream, outs, sssp_bound_s):
+    """BFS, SSSP (bounded in time) and CC from managed memory; times from the
+    library's CUDA events, plus the wall time of the whole step."""
+    r = {}
+    t0 = time.perf_counter()
+    r["bfs_ms"] = round(E.bfs(hm, src, stream=stream, out=outs[0], time_kernels=True)[1]["ms"], 2)
+    t1 = time.perf_counter()
+    try:
+        ss = E.sssp(hm, src, stream=stream, out=outs[1], time_kernels=True, timeout_ns=int(sssp_bound_s * 1e9))[1]
+        r["sssp_ms"] = round(ss["ms"], 2)
+        r["sssp_rounds"] = ss["iterations"]
+    except E.EmogiError as ex:
+        if ex.status != E.E_TIMEOUT:
+            raise
+        r["sssp_ms"] = None
+        r["sssp_unfinished"] = f"stopped at its {sssp_bound_s} s time bound: {str(ex)[:120]}"
+        r["sssp_wall_s"] = round(time.perf_counter() - t1, 1)
+    r["cc_ms"] = round(E.cc(hm, stream=stream, out=outs[2], time_kernels=True)[1]["ms"], 2)
+    r["step_wall_s"] = round(time.perf_counter() - t0, 2)
+    return r
+
+
+def managed_arm(E, torch, g, srcs, stream):
+    """The UVM baseline (Sec. 5.1.2 (a): cudaMallocManaged + ReadMostly) on the
+    same graph, first with the device held to 16 GiB (a device allocation is
+    held aside so that the library's buffers, the outputs and UVM's resident
+    pages share 16 GiB, as on the paper's 16 GB GPU), then uncapped (the whole
+    graph then fits in HBM and migrates once).  Consumes g's host arrays (they
+    move into managed memory)."""
+    import graphgen as gg
+    res = {}
+    t0 = time.perf_counter()
+    mcols = to_managed(E, gg, g.cols)
+    mw = to_managed(E, gg, g.weights)
+    g.cols = g.weights = None  # the host copy is gone
+    res["move_to_managed_s"] = round(time.perf_counter() - t0, 1)
+    outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(3)]
+    try:
+        for capped in (True, False):
+            hm = E.load_csr(g.n, g.m, g.offsets, mcols, mw, placement="managed", undirected=True, borrow=True)
+            balloon = None
+            try:
+                if capped:
+                    E.bfs(hm, srcs[0], out=outs[0], stream=stream)  # the library's buffers, before the cap
+                    torch.cuda.synchronize()
+                    free, _ = torch.cuda.mem_get_info()
+                    mine = E.device_bytes_in_use() + sum(o.numel() * 4 for o in outs)
+                    keep = max(0, DEVICE_BUDGET - mine)
+                    if free > keep:
+                        balloon = torch.empty(free - keep, dtype=torch.uint8, device="cuda")
+                    torch.cuda.synchronize()
+                    free2, _ = torch.cuda.mem_get_info()
+                    res["managed_capped"] = {
+                        "cap": {"device_budget_bytes": DEVICE_BUDGET, "library_and_outputs_bytes": mine,
+                                "held_aside_bytes": 0 if balloon is None else balloon.numel(),
+                                "free_for_uvm_bytes": free2},
+                        "step": managed_step(E, hm, srcs[1], stream, outs, MANAGED_SSSP_BOUND_S)}
+                else:
+                    cold = managed_step(E, hm, srcs[1], stream, outs, 3 * MANAGED_SSSP_BOUND_S)
+                    warm = managed_step(E, hm, srcs[2], stream, outs, MANAGED_SSSP_BOUND_S)
+                    res["managed_uncapped"] = {"note": "the whole graph fits in HBM: pages migrate on first "
+                                                       "touch, then stay", "cold_step": cold, "warm_step": warm}
+            finally:
+                hm.free()
+                del balloon
+                torch.cuda.empty_cache()
+    finally:
+        del outs, mcols, mw
+    res["managed_wall_s"] = round(time.perf_counter() - t0, 1)
+    return res
+
+
 def ours(args):
+    import graphgen as gg
     import torch
 
     rank, world, local = dist_env()
+    t_start = time.perf_counter()
+    # The graph is generated before any CUDA work: its 100 GB of arrays need
+    # transparent huge pages (the GPU reads them in place, and with 64 KiB
+    # pages it needs far more address translations than it holds).  Measured
+    # on GB300: made after the CUDA context and a pinned probe buffer, the
+    # same edge list got SSSP 5.7 s instead of 1.65 s.
+    if args.workload == "kron27":
+        g, srcs, ginfo = make_kron27()
+        ginfo["huge_pages"] = gg.huge_page_report()
+    else:
+        g, srcs = make_urand24()
+        ginfo = {}
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -267,151 +533,130 @@ def ours(args):
     _build.build()
     from paper_2006_06890_gb300 import emogi as E
 
-    g, srcs = make_graph(args.n, args.degree)
-    stream = torch.cuda.Stream()
-    peaks = measured_peaks()
-    link_peak = pinned_h2d_peak_gbs(torch)
-
-    h = E.load_graph(g, placement="host")
-    outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(3)]
-
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- device-resident timing (value)
-    barrier()
-    with ClockSampler(local) as clk:
-        ms, wall, per = time_loop(torch, E, h, srcs, stream, args.steps, args.warmup, outs)
-    barrier()
-    ms, teps_edges = combine_over_ranks(ms, sum(step_teps_edges(p) for p in per), world)
-    value = teps_edges / (ms * 1e-3) / 1e9
-    expand_ms = sum(s["expand_ms"] for p in per for s in p)
-    alg_bytes = sum(step_alg_bytes(p) for p in per)
+    stream = torch.cuda.Stream()
+    peaks = measured_peaks()
+    if args.workload == "kron27":
+        E.set_device_budget(DEVICE_BUDGET)
+        t0 = time.perf_counter()
+        h = E.load_csr(g.n, g.m, g.offsets, g.cols, g.weights, placement="host", undirected=True, borrow=True)
+        ginfo["pin_s"] = round(time.perf_counter() - t0, 1)
+        factors = LINK_BYTES_PER_ALG_BYTE["kron"]
+    else:
+        h = E.load_graph(g, placement="host")
+        factors = LINK_BYTES_PER_ALG_BYTE["urand"]
+    link_peak = pinned_h2d_peak_gbs(torch)
+
+    hl = headline(torch, E, h, g, srcs, stream, args, world, barrier)
+    per = hl["per"]
     launches = sum(s["kernel_launches"] for p in per for s in p)
-    achieved = alg_bytes / (expand_ms * 1e-3) / 1e9
-    per_alg = {}
-    for i, nm in enumerate(("bfs", "sssp", "cc")):
-        e = sum(p[i]["edges_reached"] for p in per)
-        t = sum(p[i]["ms"] for p in per)
-        per_alg[nm] = {"gteps": round(e / (t * 1e-3) / 1e9, 3), "ms_mean": round(t / len(per), 3),
-                       "iterations_mean": round(sum(p[i]["iterations"] for p in per) / len(per), 2),
-                       "edges_scanned_over_reached": round(sum(p[i]["edges_scanned"] for p in per) / max(e, 1), 3)}
-
-    # ---- end to end through the public API with host output buffers: pinned
-    # host arrays (as a serving caller keeps them), so each result crosses to
-    # the host by DMA; pageable arrays are timed too
-    e2e_steps = max(2, args.steps // 2)
-    host_outs = [torch.empty(g.n, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32) for _ in range(3)]
-    barrier()
-    ms_e2e, wall_e2e, per_e2e = time_loop(torch, E, h, srcs, stream, e2e_steps, 1, host_outs)
-    barrier()
-    ms_e2e, e2e_edges = combine_over_ranks(ms_e2e, sum(step_teps_edges(p) for p in per_e2e), world)
-    e2e_value = e2e_edges / (ms_e2e * 1e-3) / 1e9
-    barrier()
-    ms_pg, _, per_pg = time_loop(torch, E, h, srcs, stream, e2e_steps, 1, None)
-    barrier()
-    ms_pg, pg_edges = combine_over_ranks(ms_pg, sum(step_teps_edges(p) for p in per_pg), world)
-    e2e_pageable = pg_edges / (ms_pg * 1e-3) / 1e9
-    del host_outs
-
+    cfg = workload_config(args.workload, g.m)
     result = {
-        "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "metric": METRIC, "value": round(hl["value"], 4), "unit": "GTEPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(hl["ms"] / args.steps, 3),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 (integer)",
-        "data": "synthetic (seeded uniform-random graph, graphgen)",
-        "config": workload_config(g, args.n, args.degree, {"parallelism": "replicas" if world > 1 else "single"}),
-        "per_algorithm": per_alg,
-        "e2e": {"value": round(e2e_value, 4), "unit": "GTEPS", "steps": e2e_steps,
-                "h2d_bytes_per_step": 2 * 8, "d2h_bytes_per_step": 3 * 4 * g.n,
-                "note": "public API with pinned host output arrays: each call copies its n-entry result to the host",
-                "pageable_outputs_value": round(e2e_pageable, 4)},
+        "data": f"synthetic (seeded {'Kronecker' if args.workload == 'kron27' else 'uniform-random'} graph, graphgen)",
+        "config": cfg, "graph": ginfo, "per_algorithm": per_algorithm(per), "e2e": hl["e2e"],
         "gpu_launches": int(launches),
-        "roofline": {"bound": "host_link",
-                     "kernel": "expansion launches: k_expand_group / k_expand_split (BFS top-down, CC final), "
-                               "k_bfs_bottom_up, k_cc_sample, and the recorded SSSP loop (k_sssp_loop_*)",
-                     "achieved": round(achieved, 2), "peak": round(link_peak, 2), "unit": "GB/s",
-                     "frac": round(achieved / link_peak, 4),
-                     "traffic": int(sum(step_link_bytes(p) for p in per) / len(per)),
-                     "traffic_note": "host-link read bytes per step of the expansion kernels: ncu sysmem read "
-                                     "sectors x 32 per list entry on the 2^22 case (BFS 1.130, SSSP 1.135 per "
-                                     "algorithmic byte), scaled by this run's entries",
-                     "link_frac": round(sum(step_link_bytes(p) for p in per) / (expand_ms * 1e-3) / 1e9 / link_peak, 4),
-                     "peak_source": "pinned host->device cudaMemcpy, 1 GiB, best of 6, measured in this run",
-                     "algorithmic_bytes_per_step": int(alg_bytes / len(per)),
-                     "unit_bytes": "8 B per list entry read (BFS, CC), 12 B (SSSP)",
-                     "expand_ms_per_step": round(expand_ms / len(per), 3),
-                     "hbm_peak_measured_gbs": peaks.get("hbm_gbs")},
-        "clocks": clk.summary(),
-        "wall_s_timed": round(wall, 3),
+        "roofline": roofline(per, link_peak, factors, peaks, KERNEL_NOTE),
+        "clocks": hl["clocks"], "wall_s_timed": round(hl["wall"], 3),
     }
+    if args.workload == "kron27":
+        result["device_bytes_in_use"] = E.device_bytes_in_use()
 
-    # ---- comparison points on the same GPU (one timed step each)
-    if not args.no_variants and rank == 0:
+    if rank == 0 and not args.no_variants and args.workload == "kron27":
+        outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(3)]
         variants = {}
-        for name, kw in (("naive_zero_copy", dict(placement="host", access="naive")),
-                         ("merged_zero_copy", dict(placement="host", access="merged")),
-                         ("aligned_zero_copy_paper_forms", dict(placement="host", access="merged_aligned",
-                                                                top_down_only=True, cc_full_pass=True)),
-                         ("aligned_zero_copy_beamer_rule", dict(placement="host", access="merged_aligned",
-                                                                beamer=True)),
-                         ("aligned_zero_copy_ids32", dict(placement="host", access="merged_aligned", ids32=True)),
-                         ("managed_uvm", dict(placement="managed", access="merged_aligned")),
-                         ("device_hbm", dict(placement="device", access="merged_aligned")),
-                         ("device_hbm_ids32", dict(placement="device", access="merged_aligned", ids32=True))):
-            try:
-                ids32 = kw.get("ids32", False)
-                hv = h if (kw["placement"] == "host" and not ids32) else \
-                    E.load_graph(g, placement=kw["placement"], ids32=ids32)
-                okw = {k: v for k, v in kw.items() if k not in ("placement", "ids32")}
-
-                def one(src):
-                    sb = E.bfs(hv, src, stream=stream, out=outs[0], **okw)[1]
-                    ss = E.sssp(hv, src, stream=stream, out=outs[1], **okw)[1]
-                    sc = E.cc(hv, stream=stream, out=outs[2], **okw)[1]
-                    return (sb, ss, sc)
-
-                t0 = time.perf_counter()
-                first = one(srcs[0])  # cold for managed: pages migrate
-                cold_s = time.perf_counter() - t0
-                sts = [one(x) for x in srcs[1:1 + VARIANT_STEPS]]
-                tot_ms = sum(s["ms"] for st in sts for s in st)
-                edges = sum(step_teps_edges(st) for st in sts)
-                k = len(sts)
-                variants[name] = {"gteps": round(edges / (tot_ms * 1e-3) / 1e9, 4),
-                                  "ms_per_step": round(tot_ms / k, 3), "first_step_s": round(cold_s, 3),
-                                  "steps": k,
-                                  "bfs_ms": round(sum(st[0]["ms"] for st in sts) / k, 3),
-                                  "sssp_ms": round(sum(st[1]["ms"] for st in sts) / k, 3),
-                                  "cc_ms": round(sum(st[2]["ms"] for st in sts) / k, 3)}
-                del first
-                if hv is not h:
-                    hv.free()
-            except Exception as ex:  # noqa: BLE001 - report, keep the bench line
-                variants[name] = {"error": str(ex)[:200]}
+        try:
+            variants["aligned_zero_copy_paper_forms"] = variant_steps(
+                E, h, srcs[1:3], stream, outs, dict(top_down_only=True, cc_full_pass=True))
+        except Exception as ex:  # noqa: BLE001 - report, keep the bench line
+            variants["aligned_zero_copy_paper_forms"] = {"error": str(ex)[:200]}
+        del outs
+        h.free()
+        h = None
+        try:
+            variants.update(managed_arm(E, torch, g, srcs, stream))
+        except Exception as ex:  # noqa: BLE001
+            variants["managed"] = {"error": str(ex)[:300]}
         result["variants"] = variants
+    if h is not None:
+        h.free()
+    E.set_device_budget(0)
+    del g
 
-    # ---- multi-source BFS, batched many-graph BFS and serving (rank 0)
+    c2 = None
     if rank == 0 and not args.no_extras:
-        for name, fn in (("kron16_bfs", extra_kron16), ("pagerank", lambda E_, t_: extra_pagerank(E_, t_, g)),
+        try:
+            c2, result["c2"] = block_c2(E, torch, args, link_peak, peaks, stream)
+        except Exception as ex:  # noqa: BLE001
+            result["c2"] = {"error": str(ex)[:300]}
+        for name, fn in (("kron16_bfs", extra_kron16),
+                         ("pagerank", (lambda E_, t_: extra_pagerank(E_, t_, c2)) if c2 is not None else None),
                          ("msbfs", extra_msbfs), ("batch", extra_batch), ("serving", extra_serving)):
+            if fn is None:
+                continue
             try:
                 result[name] = fn(E, torch)
             except Exception as ex:  # noqa: BLE001 - report, keep the bench line
                 result[name] = {"error": str(ex)[:300]}
+    del c2
 
-    # ---- CPU oracle on a bounded sample (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(g, srcs[0])
-
-    h.free()
+        result["cpu_baseline"] = cpu_baseline(args.workload)
+    result["wall_s_total"] = round(time.perf_counter() - t_start, 1)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def block_c2(E, torch, args, link_peak, peaks, stream):
+    """The uniform 2^24, degree-32 workload (SSSP and CC, with BFS added) from
+    pinned host memory: its own timed loop and roofline, and the comparison
+    variants on the same GPU (naive, merged, the paper's forms, Beamer's rule,
+    4-byte ids, managed memory that fits in HBM, all in HBM)."""
+    g, srcs = make_urand24()
+    res = {"workload": f"uniform n=2^24 degree 32 (m={g.m}), edges + weights in pinned host memory"}
+    with E.load_graph(g, placement="host") as h:
+        outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for _ in range(3)]
+        steps = 8
+        ms, _, per = time_loop(torch, E, h, srcs, stream, steps, 2, outs)
+        res.update({"value": round(sum(step_teps_edges(p) for p in per) / (ms * 1e-3) / 1e9, 4), "unit": "GTEPS",
+                    "steps": steps, "ms_per_step": round(ms / steps, 3), "per_algorithm": per_algorithm(per),
+                    "roofline": roofline(per, link_peak, LINK_BYTES_PER_ALG_BYTE["urand"], peaks, KERNEL_NOTE)})
+        if not args.no_variants:
+            variants = {}
+            for name, kw in (("naive_zero_copy", dict(placement="host", access="naive")),
+                             ("merged_zero_copy", dict(placement="host", access="merged")),
+                             ("aligned_zero_copy_paper_forms", dict(placement="host", access="merged_aligned",
+                                                                    top_down_only=True, cc_full_pass=True)),
+                             ("aligned_zero_copy_beamer_rule", dict(placement="host", access="merged_aligned",
+                                                                    beamer=True)),
+                             ("aligned_zero_copy_ids32", dict(placement="host", access="merged_aligned",
+                                                              ids32=True)),
+                             ("managed_uvm", dict(placement="managed", access="merged_aligned")),
+                             ("device_hbm", dict(placement="device", access="merged_aligned")),
+                             ("device_hbm_ids32", dict(placement="device", access="merged_aligned", ids32=True))):
+                try:
+                    ids32 = kw.get("ids32", False)
+                    hv = h if (kw["placement"] == "host" and not ids32) else \
+                        E.load_graph(g, placement=kw["placement"], ids32=ids32)
+                    okw = {k: v for k, v in kw.items() if k not in ("placement", "ids32")}
+                    variants[name] = variant_steps(E, hv, srcs[1:1 + VARIANT_STEPS], stream, outs, okw)
+                    if hv is not h:
+                        hv.free()
+                except Exception as ex:  # noqa: BLE001 - report, keep the bench line
+                    variants[name] = {"error": str(ex)[:200]}
+            res["variants"] = variants
+        del outs
+    return g, res
 
 
 def _time(torch, fn, stream):
@@ -531,102 +776,162 @@ def extra_batch(E, torch):
             "speedup_vs_single": round(ms_s / ms_b, 3)}
 
 
+SERVING_LOADS = (1000, 2000, 5000, 10000, 20000, 50000)
+SERVING_QUERIES = 2000  # per offered load
+
+
 def extra_serving(E, torch):
-    """Poisson-arriving BFS (80 %) and SSSP (20 %) queries with seeded random
-    sources over a resident set (Kronecker scales 16, 18, 20 and uniform 2^18,
-    2^20, degree 16; the two smallest in HBM, the rest in pinned host memory),
-    results discarded; p50/p99 latency and throughput per offered load, next
-    to the same queries run one at a time."""
+    """Serving: Poisson-arriving BFS (80 %) and SSSP (20 %) queries with seeded
+    random sources over a resident set of 8 graphs (Kronecker scales 18, 20,
+    22, 24, 26 with edge factor 16 and uniform 2^20, 2^22, 2^24 with degree 16;
+    graphs of 2^22 vertices or fewer in HBM, the others borrowed in pinned
+    host memory), each query on a graph drawn uniformly, results discarded.
+    Per offered load: achieved queries/s, p50/p99 latency (arrival -> result,
+    overall and per kind), mean batch, the host-link bytes of the list
+    entries read from host-placed graphs per second, and where the slots'
+    time went; next to the same kind of queries run one at a time."""
     import graphgen as gg
-    specs = [("kron16", lambda: gg.kronecker(16, 16, seed=11, weights=True), "device"),
-             ("urand18", lambda: gg.uniform(1 << 18, 16, seed=12, weights=True), "device"),
-             ("kron18", lambda: gg.kronecker(18, 16, seed=13, weights=True), "host"),
-             ("kron20", lambda: gg.kronecker(20, 16, seed=14, weights=True), "host"),
-             ("urand20", lambda: gg.uniform(1 << 20, 16, seed=15, weights=True), "host")]
-    gs, hs = [], []
-    for _, mk, place in specs:
-        g = mk()
-        gs.append(g)
-        hs.append(E.load_graph(g, placement=place))
-    rng = np.random.default_rng(3)
-    out = {"workload": "resident set " + ", ".join(f"{nm} ({pl})" for nm, _, pl in specs)}
+    specs = [("kron18", lambda: gg.kronecker(18, 16, seed=11, weights=True), "device"),
+             ("kron20", lambda: gg.kronecker(20, 16, seed=12, weights=True), "device"),
+             ("kron22", lambda: gg.kronecker(22, 16, seed=13, weights=True), "device"),
+             ("kron24", lambda: gg.kronecker(24, 16, seed=14, weights=True), "host"),
+             ("kron26", lambda: gg.kronecker(26, 16, seed=15, weights=True), "host"),
+             ("urand20", lambda: gg.uniform(1 << 20, 16, seed=16, weights=True), "device"),
+             ("urand22", lambda: gg.uniform(1 << 22, 16, seed=17, weights=True), "device"),
+             ("urand24", lambda: gg.uniform(1 << 24, 16, seed=18, weights=True), "host")]
+    t0 = time.perf_counter()
+    gs, hs, places = [], [], []
+    out = {}
     try:
+        for _, mk, place in specs:
+            g = mk()
+            gs.append(g)
+            places.append(place)
+            hs.append(E.load_graph(g, placement=place, borrow=(place == "host")))
+        out["workload"] = "resident set " + ", ".join(f"{nm} (m={g.m}, {pl})" for (nm, _, pl), g in zip(specs, gs))
+        out["setup_s"] = round(time.perf_counter() - t0, 1)
+        rng = np.random.default_rng(3)
+        degs = [g.degrees() for g in gs]
+
         def make_queries(count):
             qs = []
             for _ in range(count):
                 gi = int(rng.integers(0, len(gs)))
-                qs.append((gi, "bfs" if rng.random() < 0.8 else "sssp", int(rng.integers(0, gs[gi].n))))
+                kind = "bfs" if rng.random() < 0.8 else "sssp"
+                src = int(rng.integers(0, gs[gi].n))
+                while degs[gi][src] == 0:  # a source with at least one edge
+                    src = int(rng.integers(0, gs[gi].n))
+                qs.append((gi, kind, src))
             return qs
 
+        def link_bytes(gi, kind, scanned):
+            return scanned * (12 if kind == "sssp" else 8) if places[gi] == "host" else 0
+
+        def summarise(qs, lat, runs, scanned, wall, slots=1):
+            lat = np.asarray(lat)
+            kinds = np.array([k for _, k, _ in qs])
+            r = {"queries": len(qs), "queries_per_s": round(len(qs) / wall, 1),
+                 "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                 "link_gbs": round(sum(link_bytes(gi, k, sc) for (gi, k, _), sc in zip(qs, scanned)) / wall / 1e9, 2)}
+            for kind in ("bfs", "sssp"):
+                sel = kinds == kind
+                if sel.any():
+                    r[kind] = {"p50_ms": round(float(np.percentile(lat[sel], 50)), 3),
+                               "p99_ms": round(float(np.percentile(lat[sel], 99)), 3),
+                               "slot_time_share": round(float(np.sum(np.asarray(runs)[sel])) /
+                                                        max(float(np.sum(runs)), 1e-9), 3)}
+            r["slot_busy"] = round(float(np.sum(runs)) / 1e3 / (wall * slots), 3)
+            return r
+
         # one query at a time through the plain calls
-        base_q = make_queries(300)
         st = torch.cuda.Stream()
         outs = [torch.empty(g.n, dtype=torch.int32, device="cuda") for g in gs]
-        t0 = time.perf_counter()
-        lat = []
+        base_q = make_queries(400)
+        for gi, kind, src in base_q[:16]:  # warm-up: every graph's buffers and loop graphs
+            (E.bfs if kind == "bfs" else E.sssp)(hs[gi], src, out=outs[gi], stream=st)
+        lat, runs, scanned = [], [], []
+        tb = time.perf_counter()
         for gi, kind, src in base_q:
             t1 = time.perf_counter()
-            (E.bfs if kind == "bfs" else E.sssp)(hs[gi], src, out=outs[gi], stream=st)
+            _, s_ = (E.bfs if kind == "bfs" else E.sssp)(hs[gi], src, out=outs[gi], stream=st)
             lat.append((time.perf_counter() - t1) * 1e3)
-        wall = time.perf_counter() - t0
-        out["one_at_a_time"] = {"queries_per_s": round(len(base_q) / wall, 1),
-                                "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                                "p99_ms": round(float(np.percentile(lat, 99)), 3)}
+            runs.append(lat[-1])
+            scanned.append(s_["edges_scanned"])
+        out["one_at_a_time"] = summarise(base_q, lat, runs, scanned, time.perf_counter() - tb)
+        del outs
         loads = []
-        with E.Server(max_slots=8) as srv:
-            for rate in (1000, 5000, 20000):
-                qs = make_queries(2000)
+        slots = 8
+        with E.Server(max_slots=slots) as srv:
+            for q in make_queries(32):  # warm-up: every worker's shares
+                srv.wait(srv.submit(hs[q[0]], q[1], q[2]))
+            for rate in SERVING_LOADS:
+                qs = make_queries(SERVING_QUERIES)
                 gaps = rng.exponential(1.0 / rate, size=len(qs))
                 tickets = []
-                t0 = time.perf_counter()
-                t_next = t0
+                tl = time.perf_counter()
+                t_next = tl
                 for (gi, kind, src), gap in zip(qs, gaps):
                     t_next += gap
                     while time.perf_counter() < t_next:
                         pass
                     tickets.append(srv.submit(hs[gi], kind, src))
                 res = [srv.wait(t) for t in tickets]
-                wall = time.perf_counter() - t0
-                lat = np.array([r["latency_ms"] for r in res])
-                loads.append({"offered_qps": rate, "achieved_qps": round(len(qs) / wall, 1),
-                              "p50_ms": round(float(np.percentile(lat, 50)), 3),
-                              "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                              "mean_batch": round(float(np.mean([r["batch_size"] for r in res])), 2),
-                              "max_batch": int(max(r["batch_size"] for r in res))})
+                wall = time.perf_counter() - tl
+                r = summarise(qs, [x["latency_ms"] for x in res], [x["run_ms"] for x in res],
+                              [x["edges_scanned"] for x in res], wall, slots)
+                r["offered_qps"] = rate
+                r["mean_batch"] = round(float(np.mean([x["batch_size"] for x in res])), 2)
+                r["max_batch"] = int(max(x["batch_size"] for x in res))
+                loads.append(r)
         out["loads"] = loads
+        out["slots"] = slots
+        out["queries_per_load"] = SERVING_QUERIES
     finally:
         for h in hs:
             h.free()
+    out["wall_s"] = round(time.perf_counter() - t0, 1)
     return out
 
 
+# The oracle's bounded sample of the scale-27 workload: the same generator
+# and edge factor at scale 23 (1/16 of the vertices and edges), so that one
+# single-threaded BFS + union-find pass takes seconds, not minutes.
+CPU_SAMPLE = dict(scale=23, ef=32)
+
+
+def cpu_sample(workload):
+    """(graph, sources, description) of the oracle's sample of a workload."""
+    import graphgen as gg
+    if workload == "kron27":
+        g = gg.kronecker(CPU_SAMPLE["scale"], CPU_SAMPLE["ef"], seed=GEN_SEED)
+        srcs = [int(s) for s in gg.random_sources(g, N_SOURCES, seed=SRC_SEED, min_degree=2)]
+        return g, srcs, (f"Kronecker scale {CPU_SAMPLE['scale']}, edge factor {CPU_SAMPLE['ef']} (n={g.n}, m={g.m}): "
+                         "the scale-27 workload's generator at 1/16 of its size")
+    g, srcs = make_urand24()
+    return g, srcs, f"the uniform 2^24 graph itself (m={g.m})"
+
+
 def oracle_step(g, src):
-    import oracle
-    t0 = time.perf_counter()
-    lv = oracle.bfs_g(g, src)
-    t1 = time.perf_counter()
-    ds = oracle.sssp_g(g, src)
-    t2 = time.perf_counter()
-    oracle.cc_g(g)
-    t3 = time.perf_counter()
-    edges = oracle.reached_edges(g.offsets, lv) + oracle.reached_edges(g.offsets, ds) + g.m
-    return edges, (t1 - t0, t2 - t1, t3 - t2)
-
-
-def cpu_baseline(g, src):
-    """The oracle's BFS and CC on the full graph (Dijkstra alone takes over a
-    minute on one core, so it is left out of this bounded sample)."""
+    """One oracle step of the bounded sample: BFS from src + union-find CC
+    (Dijkstra left out: a single-threaded heap Dijkstra over the sample takes
+    minutes)."""
     import oracle
     t0 = time.perf_counter()
     lv = oracle.bfs_g(g, src)
     t1 = time.perf_counter()
     oracle.cc_g(g)
     t2 = time.perf_counter()
-    edges = oracle.reached_edges(g.offsets, lv) + g.m
-    tot = t2 - t0
+    return oracle.reached_edges(g.offsets, lv) + g.m, (t1 - t0, t2 - t1)
+
+
+def cpu_baseline(workload="kron27"):
+    """The oracle's BFS and CC, single-threaded, on a bounded sample."""
+    g, srcs, desc = cpu_sample(workload)
+    edges, (tb, tc) = oracle_step(g, srcs[0])
+    tot = tb + tc
     return {"value": round(edges / tot / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
-            "sample": f"BFS from vertex {src} + union-find CC on the full graph, single-threaded C; "
-                      f"{tot:.1f} s (bfs {t1 - t0:.1f}, cc {t2 - t1:.1f})"}
+            "sample": f"BFS from vertex {srcs[0]} + union-find CC on {desc}; single-threaded C; "
+                      f"{tot:.1f} s (bfs {tb:.1f}, cc {tc:.1f})"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -647,7 +952,7 @@ def reference(args):
     import oracle
     oracle.build_lib()
     global _REF_GRAPH
-    g, srcs = make_graph(args.n, args.degree)
+    g, srcs, desc = cpu_sample(args.workload)
     _REF_GRAPH = g
     cores = min(os.cpu_count() or 1, max(1, args.steps), 16)
     # no GPU is touched in this process, so forking is safe
@@ -662,13 +967,16 @@ def reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 5), "unit": "GTEPS", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(wall * 1e3 / args.steps, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32/u64 (integer)",
-           "data": "synthetic (seeded uniform-random graph, graphgen)",
-           "config": workload_config(g, args.n, args.degree),
+           "data": "synthetic (seeded graph, graphgen)",
+           "config": workload_config(args.workload, read_kron27_sources().get("m") if args.workload == "kron27"
+                                     else g.m),
            "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": cores, "kind": "oracle",
-                            "sample": f"{args.steps} full steps (BFS + Dijkstra + union-find CC), one per "
-                                      f"process, {cores} processes in parallel"},
+                            "sample": f"{args.steps} steps, each the oracle's BFS from one seeded vertex + "
+                                      f"union-find CC on {desc}; one step per process, {cores} processes "
+                                      "in parallel"},
            "e2e": {"value": round(value, 5), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-           "note": "the paper publishes no implementation; the reference arm is the CPU oracle"}
+           "note": "the paper publishes no implementation; the reference arm is the CPU oracle on a bounded "
+                   "sample of the workload"}
     print(json.dumps(out), flush=True)
 
 
@@ -689,11 +997,11 @@ def ncu_case(args):
         print(json.dumps({"ncu_case": "msbfs Kronecker scale 22 ef 16, 64 sources, host", "stats": st}))
         return
     if args.ncu_case == "pagerank":
-        g, _ = make_graph(1 << 22, args.degree)
+        g, _ = make_urand24(1 << 22, URAND24["degree"])
         out = torch.empty(g.n, dtype=torch.float64, device="cuda")
         with E.load_graph(g, placement="host", with_weights=False) as h:
             st = E.pagerank(h, 0.85, tol=0.0, max_iters=3, out=out)[1]
-        print(json.dumps({"ncu_case": f"PageRank, 3 iterations, uniform n=2^22 degree {args.degree}, host", "stats": st}))
+        print(json.dumps({"ncu_case": "PageRank, 3 iterations, uniform n=2^22 degree 32, host", "stats": st}))
         return
     if args.ncu_case == "batch":
         rng = np.random.default_rng(4)
@@ -705,73 +1013,45 @@ def ncu_case(args):
             h.free()
         print(json.dumps({"ncu_case": "batched BFS, 128 uneven uniform graphs, device", "stats": st}))
         return
-    g, srcs = make_graph(1 << 22, args.degree)
+    if args.ncu_case == "access":
+        # the request-size ladder of Sec. 5.3.1: the same top-down BFS with a
+        # thread per list (naive), a warp per list (merged) and aligned groups
+        g, srcs = make_urand24(1 << 22, URAND24["degree"])
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        res = {}
+        with E.load_graph(g, placement="host", with_weights=False) as h:
+            for acc in ("naive", "merged", "merged_aligned"):
+                res[acc] = E.bfs(h, srcs[0], out=out, access=acc, top_down_only=True)[1]
+        print(json.dumps({"ncu_case": "top-down BFS, uniform n=2^22 degree 32, host, three access patterns",
+                          **res}))
+        return
+    if args.ncu_case == "kron":
+        g = gg.kronecker(23, 32, seed=GEN_SEED, weights=True)
+        srcs = [int(s) for s in gg.random_sources(g, 2, seed=SRC_SEED, min_degree=2)]
+        what = f"Kronecker scale 23 ef 32 (m={g.m}), host placement"
+    else:
+        g, srcs = make_urand24(1 << 22, URAND24["degree"])
+        what = "uniform n=2^22 degree 32, host placement"
     out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+
+    def mark(what):  # separates the calls in a per-sweep trace (EMOGI_TRACE=1)
+        print(f"=== {what}", file=sys.stderr, flush=True)
+
     with E.load_graph(g, placement="host") as h:
+        mark("bfs")
         sb = E.bfs(h, srcs[0], out=out)[1]
+        mark("sssp")
         ss = E.sssp(h, srcs[0], out=out)[1]
+        mark("sssp_host_loop")
         sh = E.sssp(h, srcs[0], out=out, host_loop=True)[1]  # sweeps as separate launches, for per-kernel counters
+        mark("cc")
         sc = E.cc(h, out=out)[1]
-    print(json.dumps({"ncu_case": f"uniform n=2^22 degree {args.degree}, host placement",
-                      "bfs": sb, "sssp": ss, "sssp_host_loop": sh, "cc": sc}))
-
-
-def kron27(args):
-    """The paper's scale: a graph whose edge list and weights do not fit a
-    16 GB device (the budget the paper's A100 runs were held to).  Edges and
-    weights are generated in place and pinned where they are (BORROW, no
-    copy); vertex state and offsets stay within the 16 GB device budget."""
-    import torch
-    from paper_2006_06890_gb300 import _build
-    _build.build()
-    from paper_2006_06890_gb300 import emogi as E
-    import graphgen as gg
-    t0 = time.perf_counter()
-    g = gg.kronecker(27, 32, seed=GEN_SEED, weights=True)
-    gen_s = time.perf_counter() - t0
-    E.set_device_budget(16 << 30)
-    srcs = [int(s) for s in gg.random_sources(g, 4, seed=SRC_SEED, min_degree=2)]
-    out = torch.empty(g.n, dtype=torch.int32, device="cuda")
-    st = torch.cuda.Stream()
-    res = {"workload": f"Kronecker scale 27 ef 32 (n={g.n}, m={g.m}), edges {g.m * 8 / 1e9:.1f} GB + weights "
-                       f"{g.m * 4 / 1e9:.1f} GB pinned in place in host memory, 16 GB device budget",
-           "generation_s": round(gen_s, 1)}
-    t0 = time.perf_counter()
-    h = E.load_csr(g.n, g.m, g.offsets, g.cols, g.weights, placement="host", undirected=True, borrow=True)
-    res["load_s"] = round(time.perf_counter() - t0, 1)
-    try:
-        link_peak = pinned_h2d_peak_gbs(torch)
-        runs = {"bfs": [], "sssp": [], "cc": []}
-        E.bfs(h, srcs[0], out=out, stream=st)
-        for s_ in srcs:
-            runs["bfs"].append(E.bfs(h, s_, out=out, stream=st, time_kernels=True)[1])
-            runs["sssp"].append(E.sssp(h, s_, out=out, stream=st, time_kernels=True)[1])
-        runs["cc"].append(E.cc(h, out=out, stream=st, time_kernels=True)[1])
-        runs["cc"].append(E.cc(h, out=out, stream=st, time_kernels=True)[1])
-        for nm, lst in runs.items():
-            ms = float(np.mean([x["ms"] for x in lst]))
-            reached = float(np.mean([x["edges_reached"] for x in lst]))
-            scanned = float(np.mean([x["edges_scanned"] for x in lst]))
-            ub = 12 if nm == "sssp" else 8
-            res[nm] = {"ms_mean": round(ms, 2), "gteps": round(reached / (ms * 1e-3) / 1e9, 3),
-                       "edges_scanned_over_reached": round(scanned / max(reached, 1), 4),
-                       "link_gbs_useful": round(ub * scanned / (float(np.mean([x["expand_ms"] for x in lst])) * 1e-3)
-                                                / 1e9, 1)}
-        res["link_peak_gbs"] = round(link_peak, 1)
-        res["device_bytes_in_use"] = E.device_bytes_in_use()
-        _, tdo = E.bfs(h, srcs[0], out=out, stream=st, top_down_only=True)
-        res["bfs_top_down_only_ms"] = round(tdo["ms"], 2)
-    finally:
-        h.free()
-        E.set_device_budget(0)
-    print(json.dumps({"workload_extra": "kron27", **res}), flush=True)
+    print(json.dumps({"ncu_case": what, "bfs": sb, "sssp": ss, "sssp_host_loop": sh, "cc": sc}))
 
 
 def main():
     args = parse()
-    if args.workload == "kron27":
-        kron27(args)
-    elif args.ncu_case:
+    if args.ncu_case:
         ncu_case(args)
     elif args.impl == "reference":
         reference(args)

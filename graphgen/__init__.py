@@ -93,6 +93,31 @@ def aligned_empty(count: int, dtype, align: int = 4096) -> np.ndarray:
     return raw[off:off + nbytes].view(dtype)[:int(count)]
 
 
+def huge_page_report() -> dict:
+    """Transparent huge page settings and this process's anonymous memory on
+    huge pages (from /proc), for reports beside measurements of arrays that a
+    GPU reads in place: with 64 KiB pages a tens-of-GB edge list needs far
+    more address translations than the GPU holds."""
+    out = {}
+    for name in ("enabled", "defrag"):
+        try:
+            with open(f"/sys/kernel/mm/transparent_hugepage/{name}") as f:
+                txt = f.read().strip()
+            out[name] = txt[txt.index("[") + 1:txt.index("]")] if "[" in txt else txt
+        except (OSError, ValueError):
+            out[name] = None
+    out["huge_page_bytes"] = _huge_page_bytes()
+    try:
+        with open("/proc/self/smaps_rollup") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k in ("Anonymous", "AnonHugePages"):
+                    out[k.lower() + "_bytes"] = int(v.split()[0]) * 1024
+    except OSError:
+        pass
+    return out
+
+
 def release_host_range(arr: np.ndarray, lo: int, hi: int) -> int:
     """Return the physical pages wholly inside elements [lo, hi) of a 1-D
     array to the operating system (madvise MADV_DONTNEED; for anonymous

@@ -60,10 +60,13 @@ typedef enum {
 /* emogi_load_csr flags */
 enum {
     EMOGI_LOAD_UNDIRECTED = 1u << 0, /* caller asserts the CSR is symmetric; required by emogi_cc */
-    EMOGI_LOAD_BORROW = 1u << 1,     /* HOST only: pin and map the caller's arrays in place, no copy */
-    EMOGI_LOAD_NO_HEADS = 1u << 2    /* HOST / MANAGED: do not mirror the first 4 ids of every list in
-                                        GPU memory (16 bytes per vertex; sampled CC and bottom-up BFS
-                                        read them there instead of over the host link) */
+    EMOGI_LOAD_BORROW = 1u << 1,     /* HOST: pin and map the caller's arrays in place, no copy;
+                                        MANAGED: use the caller's managed arrays in place */
+    EMOGI_LOAD_NO_HEADS = 1u << 2    /* HOST / MANAGED: do not mirror the first 4 ids of every list (and,
+                                        with weights, their weights) in GPU memory (16 bytes per vertex,
+                                        32 with weights; sampled CC and bottom-up BFS read them there, and
+                                        lists of at most 4 entries are read from there whole, instead of
+                                        over the host link) */
 };
 
 /* How a worker reads one neighbour list (Sec. 4.2, Sec. 4.3, Listings
@@ -126,8 +129,10 @@ typedef struct {
     uint32_t reserved;
     uint64_t edges_scanned; /* neighbour-list entries read by the expansion kernels */
     uint64_t edges_reached; /* sum of out-degrees of reached vertices (the TEPS numerator; m for CC) */
-    uint64_t edge_bytes;    /* edges_scanned * bytes per id (8, or 4 for emogi_load_csr32) */
-    uint64_t weight_bytes;  /* weights read (SSSP): edges_scanned * 4 */
+    uint64_t edge_bytes;    /* bytes of ids read from the edge list: the entries of edges_scanned not
+                               served by the list heads in GPU memory, * bytes per id (8, or 4 for
+                               emogi_load_csr32) */
+    uint64_t weight_bytes;  /* weights read from the weight array (SSSP): those entries * 4 */
     double ms;              /* device time of the traversal, CUDA events on the launch stream */
     double expand_ms;       /* with EMOGI_OPT_TIME_KERNELS: summed duration of expansion launches */
     uint64_t expand_launches; /* neighbour-expansion sweeps */
@@ -146,9 +151,15 @@ typedef struct {
  *   place        emogi_placement of col_idx and weights
  *   flags        EMOGI_LOAD_* bits
  *   out          receives the handle; release it with emogi_free_graph
- * With EMOGI_LOAD_BORROW (HOST only) the library registers col_idx and weights
- * with cudaHostRegister instead of copying; they must be 16-byte aligned and
- * the caller must keep them alive and unchanged until emogi_free_graph.
+ * With EMOGI_LOAD_BORROW and EMOGI_PLACE_HOST the library registers col_idx
+ * and weights with cudaHostRegister instead of copying; they must be 16-byte
+ * aligned and the caller must keep them alive and unchanged until
+ * emogi_free_graph.  With EMOGI_LOAD_BORROW and EMOGI_PLACE_MANAGED, col_idx
+ * and weights must be managed memory (cudaMallocManaged, e.g. from
+ * emogi_managed_alloc), 16-byte aligned; the library advises them read-mostly
+ * and reads them in place (a graph larger than the host can hold twice then
+ * needs no second copy); the caller frees them after emogi_free_graph.  A
+ * borrowed DEVICE placement is rejected (EMOGI_E_ARG).
  * The GPU reads a borrowed list wherever it lies, so large borrowed arrays
  * should sit on huge pages (e.g. an anonymous mapping advised with
  * MADV_HUGEPAGE before it is filled): with 64 KiB pages a 50 GB edge list
@@ -334,6 +345,8 @@ typedef struct {
     double run_ms;           /* job start -> result ready */
     double latency_ms;       /* submit -> result ready */
     uint64_t edges_reached;  /* TEPS numerator (a batch reports its mean per query) */
+    uint64_t edges_scanned;  /* list entries the job read (a batch reports its total divided by its
+                                queries, so the sum over a batch's queries is what the pass read) */
 } emogi_query_result;
 emogi_status emogi_server_create(const emogi_server_config* cfg, emogi_server* out);
 emogi_status emogi_server_submit(emogi_server s, emogi_graph g, uint32_t kind, uint64_t src, uint32_t* out,
@@ -351,6 +364,16 @@ emogi_status emogi_set_device_budget(uint64_t bytes);
 
 /* Bytes of device memory the library currently holds (graphs + work buffers). */
 uint64_t emogi_device_bytes_in_use(void);
+
+/* Managed (UVM) memory for arrays that a caller fills on the host and then
+ * loads with EMOGI_PLACE_MANAGED | EMOGI_LOAD_BORROW (the UVM baseline of
+ * Sec. 5.1.2 (a) without a second copy of the edge list).  The pages live in
+ * host memory until the GPU touches them; they are not counted against the
+ * device budget.  emogi_managed_alloc returns a 256-byte aligned pointer, or
+ * EMOGI_E_ARG (out NULL or bytes 0) / EMOGI_E_NOMEM; emogi_managed_free(NULL)
+ * is a no-op, and the memory must not be freed while a graph borrows it. */
+emogi_status emogi_managed_alloc(uint64_t bytes, void** out);
+emogi_status emogi_managed_free(void* p);
 
 /* Release a graph and every buffer the library holds for it.  NULL is a no-op.
  * Returns EMOGI_E_CUDA if a CUDA free failed (the handle is released anyway). */

@@ -457,6 +457,9 @@ emogi_status emogi_batch_create(const emogi_graph* graphs, uint32_t count, emogi
     if (e == cudaSuccess) e = cudaEventCreate(&b->ev[1]);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_graphs, table.data(), count * sizeof(BatchGraph), cudaMemcpyHostToDevice);
+    // the copy ran on the legacy default stream, which the batch's non-blocking
+    // stream does not wait for: finish it before the batch is handed out
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
     if (e != cudaSuccess) return bail(fail(EMOGI_E_CUDA, "batch set-up: %s", cudaGetErrorString(e)));
     double deg = 0.0;
     for (auto* gr : b->graphs) deg += gr->avg_degree;

@@ -148,6 +148,9 @@ emogi_status ensure_workspace(emogi_graph g) {
     if (e == cudaSuccess) e = cudaMemset(ws.qround, 0, n * 4);
     if (e == cudaSuccess) e = cudaMemset(ws.fflag, 0, n * 4);
     if (e == cudaSuccess) e = cudaMemset(ws.nflag, 0, (n / 16 + 1) * 16);
+    // cudaMemset runs on the legacy default stream, which the traversals'
+    // non-blocking streams do not wait for: finish it before any of them starts
+    if (e == cudaSuccess) e = cudaStreamSynchronize(cudaStreamLegacy);
     for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaEventCreate(&ws.ev[i]);
     if (e != cudaSuccess) {
         release_workspace(g);
@@ -294,8 +297,26 @@ static emogi_status place_array(int place, bool borrow, int device, const void* 
         *kernel_ptr = p;
         *owned = p;
         *dev_bytes += alloc;
-    } else if (place == EMOGI_PLACE_HOST && borrow && bytes == 0) {
+    } else if (borrow && bytes == 0) {
         *kernel_ptr = src;  // nothing to pin; kernels never dereference an empty list
+    } else if (place == EMOGI_PLACE_MANAGED && borrow) {
+        // the caller's managed array, used in place with the baseline's
+        // read-mostly advice (the UVM baseline of Sec. 5.1.2 (a))
+        if (((uintptr_t)src) % 16)
+            return fail(EMOGI_E_ARG, "%s: borrowed arrays must be 16-byte aligned", what);
+        cudaPointerAttributes at;
+        cudaError_t e = cudaPointerGetAttributes(&at, src);
+        if (e != cudaSuccess || at.type != cudaMemoryTypeManaged) {
+            cudaGetLastError();
+            return fail(EMOGI_E_ARG, "%s: a borrowed MANAGED array must come from cudaMallocManaged", what);
+        }
+        cudaMemLocation loc;
+        loc.type = cudaMemLocationTypeDevice;
+        loc.id = device;
+        e = cudaMemAdvise(src, bytes, cudaMemAdviseSetReadMostly, loc);
+        if (e != cudaSuccess) return fail(EMOGI_E_CUDA, "%s: cudaMemAdvise(ReadMostly): %s", what, cudaGetErrorString(e));
+        *kernel_ptr = src;
+        *borrowed = src;
     } else if (place == EMOGI_PLACE_HOST && borrow) {
         if (((uintptr_t)src) % 16)
             return fail(EMOGI_E_ARG, "%s: borrowed arrays must be 16-byte aligned", what);
@@ -406,9 +427,90 @@ static emogi_status build_heads(emogi_graph g, const uint64_t* off, const Id* co
     return EMOGI_OK;
 }
 
+// The short-list store: every list of 1..kShortMax entries, copied whole
+// (ids, and weights when given) into GPU memory, lists starting on 4-entry
+// boundaries; short_off[v] is the start in units of 4 entries (lists longer
+// than kShortMax or empty get 0 and are never read there).  Built on the host
+// from the caller's arrays in two parallel passes (slot counts per block of
+// vertices, then the copy), then copied to the device.
+template <class Id>
+static emogi_status build_short_store(emogi_graph g, const uint64_t* off, const Id* cols, const uint32_t* weights) {
+    const uint64_t n = g->n;
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n < 65536) nt = 1;
+    auto slots_of = [&](uint64_t v) -> uint64_t {
+        const uint64_t d = off[v + 1] - off[v];
+        return d >= 1 && d <= kShortMax ? (d + 3) / 4 * 4 : 0;
+    };
+    std::vector<uint64_t> part(nt + 1, 0);
+    {
+        std::vector<std::thread> th;
+        auto count = [&](unsigned t) {
+            uint64_t x = 0;
+            for (uint64_t v = n * t / nt; v < n * (t + 1) / nt; v++) x += slots_of(v);
+            part[t + 1] = x;
+        };
+        for (unsigned t = 1; t < nt; t++) th.emplace_back(count, t);
+        count(0);
+        for (auto& x : th) x.join();
+    }
+    for (unsigned t = 0; t < nt; t++) part[t + 1] += part[t];
+    const uint64_t slots = part[nt];
+    if (slots == 0) return EMOGI_OK;
+    if (slots / 4 >= 0xFFFFFFFFull) return EMOGI_OK;  // the uint32 index cannot address it: no store
+    std::vector<uint32_t> so, sid, sw;
+    try {
+        so.resize(n);
+        sid.assign(slots, 0xFFFFFFFFu);
+        if (weights) sw.assign(slots, 0u);
+    } catch (...) {
+        return fail(EMOGI_E_NOMEM, "short-list store staging (%llu bytes)",
+                    (unsigned long long)(n * 4 + slots * (weights ? 8 : 4)));
+    }
+    std::vector<uint64_t> ents(nt, 0);
+    {
+        std::vector<std::thread> th;
+        auto fill = [&](unsigned t) {
+            uint64_t pos = part[t], e = 0;
+            for (uint64_t v = n * t / nt; v < n * (t + 1) / nt; v++) {
+                const uint64_t k = slots_of(v);
+                so[v] = (uint32_t)(pos / 4);
+                if (!k) continue;
+                const uint64_t d = off[v + 1] - off[v];
+                for (uint64_t r = 0; r < d; r++) {
+                    sid[pos + r] = (uint32_t)cols[off[v] + r];
+                    if (weights) sw[pos + r] = weights[off[v] + r];
+                }
+                pos += k;
+                e += d;
+            }
+            ents[t] = e;
+        };
+        for (unsigned t = 1; t < nt; t++) th.emplace_back(fill, t);
+        fill(0);
+        for (auto& x : th) x.join();
+    }
+    uint64_t entries = 0;
+    for (auto e : ents) entries += e;
+    EMOGI_TRY(dev_alloc((void**)&g->d_short_off, n * 4, "short-list store index"));
+    g->dev_bytes += n * 4;
+    EMOGI_TRY(dev_alloc((void**)&g->d_short_ids, slots * 4, "short-list store ids"));
+    g->dev_bytes += slots * 4;
+    if (weights) {
+        EMOGI_TRY(dev_alloc((void**)&g->d_short_w, slots * 4, "short-list store weights"));
+        g->dev_bytes += slots * 4;
+    }
+    g->short_slots = slots;
+    g->short_entries = entries;
+    EMOGI_CUDA_TRY(cudaMemcpy(g->d_short_off, so.data(), n * 4, cudaMemcpyHostToDevice));
+    EMOGI_CUDA_TRY(cudaMemcpy(g->d_short_ids, sid.data(), slots * 4, cudaMemcpyHostToDevice));
+    if (weights) EMOGI_CUDA_TRY(cudaMemcpy(g->d_short_w, sw.data(), slots * 4, cudaMemcpyHostToDevice));
+    return EMOGI_OK;
+}
+
 static void release_array(int place, void* owned, const void* borrowed, size_t bytes) {
     size_t alloc = ((bytes + 127) / 128) * 128 + 128;
-    if (borrowed) cudaHostUnregister((void*)borrowed);
+    if (borrowed && place == EMOGI_PLACE_HOST) cudaHostUnregister((void*)borrowed);
     if (!owned) return;
     if (place == EMOGI_PLACE_DEVICE) {
         dev_free(owned, alloc);
@@ -440,7 +542,8 @@ static emogi_status load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets
     if (flags & ~(uint32_t)(EMOGI_LOAD_UNDIRECTED | EMOGI_LOAD_BORROW | EMOGI_LOAD_NO_HEADS))
         return fail(EMOGI_E_ARG, "unknown load flags 0x%x", flags);
     const bool borrow = flags & EMOGI_LOAD_BORROW;
-    if (borrow && place != EMOGI_PLACE_HOST) return fail(EMOGI_E_ARG, "EMOGI_LOAD_BORROW needs EMOGI_PLACE_HOST");
+    if (borrow && place == EMOGI_PLACE_DEVICE)
+        return fail(EMOGI_E_ARG, "EMOGI_LOAD_BORROW needs EMOGI_PLACE_HOST or EMOGI_PLACE_MANAGED");
     EMOGI_TRY(validate_csr(n, m, row_offsets, col_idx));
 
     emogi_graph g = new (std::nothrow) emogi_graph_s();
@@ -488,15 +591,26 @@ static emogi_status load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets
         if (s != EMOGI_OK) return bail(s);
         g->w = (const uint32_t*)kp;
     }
-    // list heads: the first ids of every list mirrored in GPU memory when the
-    // edge list itself is not there (16 bytes per vertex)
+    // list heads and the short-list store: when the edge list itself is not in
+    // GPU memory, the first ids of every list (16 bytes per vertex) and every
+    // list of at most kShortMax entries (ids and weights) are mirrored there
     if (place != EMOGI_PLACE_DEVICE && !(flags & EMOGI_LOAD_NO_HEADS) && n && m) {
         s = dev_alloc((void**)&g->d_heads, n * 4 * sizeof(uint32_t), "list heads");
         if (s != EMOGI_OK) return bail(s);
         g->dev_bytes += n * 4 * sizeof(uint32_t);
         s = build_heads(g, row_offsets, col_idx);
         if (s != EMOGI_OK) return bail(s);
+        s = build_short_store(g, row_offsets, col_idx, weights);
+        if (s != EMOGI_OK) return bail(s);
     }
+    // The uploads above (cudaMemcpy, from pageable host memory) run on the
+    // legacy default stream and may return before their DMA has landed; the
+    // traversals run on non-blocking streams, which do not wait for the
+    // legacy stream.  Measured on GB300: a BFS started at once after loading a
+    // 134 M-vertex graph (1 GB of offsets) read offsets still in flight and got
+    // wrong levels.  So the load returns only once every upload is complete.
+    e = cudaStreamSynchronize(cudaStreamLegacy);
+    if (e != cudaSuccess) return bail(fail(EMOGI_E_CUDA, "graph upload: %s", cudaGetErrorString(e)));
     *out = g;
     return EMOGI_OK;
 }
@@ -532,6 +646,26 @@ emogi_status emogi_set_device_budget(uint64_t bytes) {
 
 uint64_t emogi_device_bytes_in_use(void) { return g_in_use.load(); }
 
+emogi_status emogi_managed_alloc(uint64_t bytes, void** out) {
+    clear_error();
+    if (!out || bytes == 0) return fail(EMOGI_E_ARG, "emogi_managed_alloc needs out != NULL and bytes > 0");
+    *out = nullptr;
+    cudaError_t e = cudaMallocManaged(out, bytes, cudaMemAttachGlobal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return fail(EMOGI_E_NOMEM, "cudaMallocManaged(%llu): %s", (unsigned long long)bytes, cudaGetErrorString(e));
+    }
+    return EMOGI_OK;
+}
+
+emogi_status emogi_managed_free(void* p) {
+    clear_error();
+    if (!p) return EMOGI_OK;
+    EMOGI_CUDA_TRY(cudaFree(p));
+    return EMOGI_OK;
+}
+
 void emogi_test_fail_device_alloc_after(int k) { g_fail_after = k > 0 ? k : 0; }
 
 emogi_status emogi_load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets, const uint64_t* col_idx,
@@ -551,6 +685,9 @@ emogi_status emogi_free_graph(emogi_graph g) {
     release_workspace(g);
     if (!g->shared) {
         if (g->d_heads) dev_free(g->d_heads, g->n * 4 * sizeof(uint32_t));
+        if (g->d_short_off) dev_free(g->d_short_off, g->n * 4);
+        if (g->d_short_ids) dev_free(g->d_short_ids, g->short_slots * 4);
+        if (g->d_short_w) dev_free(g->d_short_w, g->short_slots * 4);
         release_array(g->place, g->cols_owned, g->cols_borrowed, g->m * g->id_bytes);
         if (g->w || g->w_owned || g->w_borrowed)
             release_array(g->place, g->w_owned, g->w_borrowed, g->m * sizeof(uint32_t));
@@ -576,6 +713,11 @@ emogi_status emogi_graph_share(emogi_graph g, emogi_graph* out) {
     h->place = g->place;
     h->d_off = g->d_off;
     h->d_heads = g->d_heads;
+    h->d_short_off = g->d_short_off;
+    h->d_short_ids = g->d_short_ids;
+    h->d_short_w = g->d_short_w;
+    h->short_slots = g->short_slots;
+    h->short_entries = g->short_entries;
     h->cols = g->cols;
     h->id_bytes = g->id_bytes;
     h->w = g->w;

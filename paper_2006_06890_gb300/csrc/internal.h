@@ -11,6 +11,11 @@
 
 namespace emogi {
 
+// Lists of at most this many entries are mirrored whole in GPU memory (the
+// short-list store) when the edge list is not there; the kernels' copy of the
+// constant is checked against this one where both are visible.
+constexpr uint64_t kShortMax = 16;
+
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
 void clear_error();
@@ -69,6 +74,7 @@ struct DevCounters {
     unsigned long long ms_active;    // MS-BFS: sources whose frontier is non-empty
     uint32_t giant;                  // sampled CC: root of the largest sampled tree
     uint32_t pad2;
+    unsigned long long scanned_heads; // of `scanned`: entries of whole lists read from the list heads in GPU memory
 };
 
 struct Workspace {
@@ -117,6 +123,14 @@ struct emogi_graph_s {
     int place = EMOGI_PLACE_DEVICE;
     uint64_t* d_off = nullptr;         // device row offsets (n + 1)
     uint32_t* d_heads = nullptr;       // first 4 ids of every list in GPU memory (edge lists off the GPU)
+    // short-list store: every list of 1..kShortMax entries copied whole to GPU
+    // memory (ids as uint32, and weights), each starting on a 4-entry boundary;
+    // d_short_off[v] = start of v's list in units of 4 entries (edge lists off the GPU)
+    uint32_t* d_short_off = nullptr;
+    uint32_t* d_short_ids = nullptr;
+    uint32_t* d_short_w = nullptr;
+    uint64_t short_slots = 0;          // entries the store holds (padding included)
+    uint64_t short_entries = 0;        // list entries it holds
     const void* cols = nullptr;        // kernel-visible edge list (uint64 or uint32 ids)
     uint32_t id_bytes = 8;             // bytes per id: 8, or 4 for a graph loaded by emogi_load_csr32
     const uint32_t* w = nullptr;       // kernel-visible weights or null

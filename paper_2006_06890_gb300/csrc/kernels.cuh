@@ -54,6 +54,10 @@ struct Sweep {
     uint32_t chunk_lines = 1;            // lines per split work item
     unsigned long long* scanned = nullptr;         // neighbour entries read (statistics)
     const uint32_t* heads = nullptr;     // first kHeads ids of every list in GPU memory, or null
+    const uint32_t* short_off = nullptr; // short-list store (see kShortMax): start of v's list / 4, or null
+    const uint32_t* short_ids = nullptr;
+    const uint32_t* short_w = nullptr;   // its weights (weighted graphs), or null
+    unsigned long long* scanned_heads = nullptr;  // entries read from the store instead of the edge list
     uint64_t m = 0;                      // entries in the edge list (and weights): a lane's 16-byte
                                          // load at index j is whole when j + ids per load <= m
     uint32_t qcap = 0xFFFFFFFFu;         // entries out_q holds: an append at or past it is dropped
@@ -62,6 +66,9 @@ struct Sweep {
 
 // Entries of each list mirrored in GPU memory ("list heads", INF-padded).
 constexpr int kHeads = 4;
+// Lists of at most kShortMax entries are mirrored whole in GPU memory (the
+// short-list store) when the edge list is not there.
+constexpr uint32_t kShortMax = 16;
 
 // ------------------------------------------------------------------ loads
 // Edge-list reads go through the non-coherent read-only path and do not
@@ -531,10 +538,14 @@ struct OverflowCheckOp {
 };
 
 // ------------------------------------------------------------------ statistics
-__device__ __forceinline__ void add_scanned(const Sweep& c, unsigned long long x) {
+__device__ __forceinline__ void add_scanned(const Sweep& c, unsigned long long x, unsigned long long xh = 0) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        x += __shfl_xor_sync(0xffffffffu, x, o);
+        xh += __shfl_xor_sync(0xffffffffu, xh, o);
+    }
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(c.scanned, x);
+    if ((threadIdx.x & 31) == 0 && xh && c.scanned_heads) atomicAdd(c.scanned_heads, xh);
 }
 
 // One 16-byte step of a list read: the lane covers ids [j, j + E) of [s, e),
@@ -626,6 +637,49 @@ __device__ __forceinline__ typename StepOf<Id>::T load_step(const Sweep& c, uint
                                                              bool active) {
     if constexpr (sizeof(Id) == 8) return load_pair<Op>(c, j, s, e, active);
     else return load_quad<Op>(c, j, s, e, active);
+}
+
+// Whole lists of at most kShortMax entries are read from the short-list store
+// in GPU memory (ids, and weights when the op reads them) instead of the edge
+// list, in the same steps a list read makes, so peek and visit are unchanged.
+// Where an edge list sits in host memory, a sweep over a sparse frontier (a
+// few of every hundred vertices, most of them of low degree, spread over the
+// whole array) lands each list read on a different part of the array, and the
+// GPU's address translations of a 100 GB array then bound it, not the link:
+// measured on GB300, Kronecker scale 27 (67 GB of ids + 33 GB of weights),
+// such SSSP sweeps read 7.5 GB/s while dense ones read 164 GB/s.  Short lists
+// are most of those reads.  A store list starts on a 4-entry boundary, so a
+// lane's two or four entries are one 8- or 16-byte load.
+template <class Op>
+__device__ __forceinline__ bool reads_store(const Sweep& c, uint64_t s, uint64_t e) {
+    return c.short_off && (!Op::kWeights || c.short_w) && e > s && e - s <= (uint64_t)kShortMax;
+}
+template <class Op, class Id>
+__device__ __forceinline__ typename StepOf<Id>::T store_step(const Sweep& c, uint32_t v, uint32_t j, uint32_t len,
+                                                              bool active) {
+    typename StepOf<Id>::T p;
+    p.valid = 0;
+    const uint64_t b = (uint64_t)c.short_off[v] * 4 + j;  // j: the lane's first entry, a multiple of E
+    if constexpr (sizeof(Id) == 8) {
+        p.id = make_ulonglong2(0, 0);
+        p.w = make_uint2(0, 0);
+        if (active && j < len) {
+            const uint2 id = *reinterpret_cast<const uint2*>(c.short_ids + b);
+            p.id = make_ulonglong2(id.x, id.y);
+            if (Op::kWeights) p.w = *reinterpret_cast<const uint2*>(c.short_w + b);
+            p.valid = 1u | (j + 1 < len ? 2u : 0u);
+        }
+    } else {
+        p.id = make_uint4(0, 0, 0, 0);
+        p.w = make_uint4(0, 0, 0, 0);
+        if (active && j < len) {
+            p.id = *reinterpret_cast<const uint4*>(c.short_ids + b);
+            if (Op::kWeights) p.w = *reinterpret_cast<const uint4*>(c.short_w + b);
+            const uint32_t k = len - j < 4 ? len - j : 4;
+            p.valid = (1u << k) - 1u;
+        }
+    }
+    return p;
 }
 
 // The neighbours' current values (level, distance) a step's updates compare
@@ -783,7 +837,7 @@ __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t k = c.in_q ? (uint64_t)*c.in_count : (uint64_t)c.all_n;
-    unsigned long long scanned = 0;
+    unsigned long long scanned = 0, scanned_h = 0;
     for (uint64_t base = warp * GPW; base < k; base += nwarps * GPW) {
         const uint64_t idx = base + grp;
         uint32_t v = 0;
@@ -800,19 +854,25 @@ __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
         }
         uint64_t a = aligned_start<Id>(s, c.shift);
         const uint64_t lines = e > s ? (e - a + LINE - 1) / LINE : 0;
-        if (glane == 0) scanned += e - s;
+        const bool hd = reads_store<Op>(c, s, e);
+        if (glane == 0) {
+            scanned += e - s;
+            if (hd) scanned_h += e - s;
+        }
         if (lines > c.large_lines) {
             if (glane == 0) defer(c, v, (lines + c.chunk_lines - 1) / c.chunk_lines, (unsigned long long)st);
             s = e = a = 0;
         }
-        const uint32_t steps = e > s ? (uint32_t)((e - a + E * G - 1) / (E * G)) : 0u;
+        const uint64_t from = hd ? s : a;  // a store list starts at its first entry
+        const uint32_t steps = e > s ? (uint32_t)((e - from + E * G - 1) / (E * G)) : 0u;
         const uint32_t maxsteps = __reduce_max_sync(0xffffffffu, steps);
         for (uint32_t t0 = 0; t0 < maxsteps; t0 += KS) {
             typename StepOf<Id>::T p[KS];
             typename CurOf<Id>::T cur[KS];
 #pragma unroll
             for (int u = 0; u < KS; u++)
-                p[u] = load_step<Op, Id>(c, a + (uint64_t)(t0 + u) * (E * G) + E * glane, s, e, t0 + u < steps);
+                p[u] = hd ? store_step<Op, Id>(c, v, (t0 + u) * (E * G) + E * glane, (uint32_t)(e - s), t0 + u < steps)
+                          : load_step<Op, Id>(c, a + (uint64_t)(t0 + u) * (E * G) + E * glane, s, e, t0 + u < steps);
 #pragma unroll
             for (int u = 0; u < KS; u++) cur[u] = peek_step(op, p[u]);
 #pragma unroll
@@ -820,7 +880,7 @@ __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
         }
     }
     if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count, c.qcap);
-    add_scanned(c, scanned);
+    add_scanned(c, scanned, scanned_h);
     op.flush();
 }
 
@@ -844,7 +904,7 @@ __global__ void __launch_bounds__(256) k_expand_all(Sweep c, Op op_in) {
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t n = c.all_n;
-    unsigned long long scanned = 0;
+    unsigned long long scanned = 0, scanned_h = 0;
     for (uint64_t base = warp * 32; base < n; base += nwarps * 32) {
         const uint64_t v = base + lane;
         typename Op::S st = Op::kSkip;
@@ -855,6 +915,7 @@ __global__ void __launch_bounds__(256) k_expand_all(Sweep c, Op op_in) {
             s = c.off[v];
             e = c.off[v + 1];
             scanned += e - s;
+            if (reads_store<Op>(c, s, e)) scanned_h += e - s;
             const uint64_t a = aligned_start<Id>(s, c.shift);
             const uint64_t lines = e > s ? (e - a + LINE - 1) / LINE : 0;
             if (lines > c.large_lines) defer(c, (uint32_t)v, (lines + c.chunk_lines - 1) / c.chunk_lines,
@@ -874,14 +935,18 @@ __global__ void __launch_bounds__(256) k_expand_all(Sweep c, Op op_in) {
             uint64_t ee = __shfl_sync(0xffffffffu, e, src);
             if (!mine) ss = ee = 0;
             const uint64_t a = aligned_start<Id>(ss, c.shift);
-            const uint32_t steps = ee > ss ? (uint32_t)((ee - a + E * G - 1) / (E * G)) : 0u;
+            const bool hd = reads_store<Op>(c, ss, ee);
+            const uint32_t steps = ee > ss ? (uint32_t)((ee - (hd ? ss : a) + E * G - 1) / (E * G)) : 0u;
             const uint32_t maxsteps = __reduce_max_sync(0xffffffffu, steps);
             for (uint32_t t0 = 0; t0 < maxsteps; t0 += KS) {
                 typename StepOf<Id>::T p[KS];
                 typename CurOf<Id>::T cur[KS];
 #pragma unroll
                 for (int u = 0; u < KS; u++)
-                    p[u] = load_step<Op, Id>(c, a + (uint64_t)(t0 + u) * (E * G) + E * glane, ss, ee, t0 + u < steps);
+                    p[u] = hd ? store_step<Op, Id>(c, vv, (t0 + u) * (E * G) + E * glane, (uint32_t)(ee - ss),
+                                                   t0 + u < steps)
+                              : load_step<Op, Id>(c, a + (uint64_t)(t0 + u) * (E * G) + E * glane, ss, ee,
+                                                  t0 + u < steps);
 #pragma unroll
                 for (int u = 0; u < KS; u++) cur[u] = peek_step(op, p[u]);
 #pragma unroll
@@ -890,13 +955,30 @@ __global__ void __launch_bounds__(256) k_expand_all(Sweep c, Op op_in) {
         }
     }
     if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count, c.qcap);
-    add_scanned(c, scanned);
+    add_scanned(c, scanned, scanned_h);
     op.flush();
 }
 
 // Split lists: work item i of vertex lq_v[slot] covers lines
-// [i * chunk_lines, (i + 1) * chunk_lines) of its aligned list; one warp per
-// item, 16 bytes per lane (four 128-byte lines per step).
+// [i * chunk_lines, (i + 1) * chunk_lines) of its aligned list.  The items of
+// all split lists (in slot order) are cut into one contiguous run per warp: a
+// warp finds the slot of its first item once (binary search over the slots'
+// first items) and then walks on item by item and list by list, 16 bytes per
+// lane and step (32 lanes: four 128-byte lines), with kSplitSteps steps of
+// loads in flight before their neighbours are read and updated.  Lists above
+// 32 lines hold most of the edges of a skewed graph (Kronecker scale 22,
+// edge factor 32: 72 %), so this path carries most of its link traffic; a
+// warp per item with a search of its own and one step in flight left it
+// latency-bound.
+#ifndef EMOGI_SPLIT_STEPS
+#define EMOGI_SPLIT_STEPS 4
+#endif
+constexpr int kSplitSteps = EMOGI_SPLIT_STEPS;
+#ifndef EMOGI_SPLIT_RUNS
+#define EMOGI_SPLIT_RUNS 1
+#endif
+
+#if !EMOGI_SPLIT_RUNS
 template <class Op, class Id = uint64_t>
 __device__ __forceinline__ void expand_split_body(const Sweep& c, Op& op) {
     constexpr int E = IdWidth<Id>::kPerStep, LINE = IdWidth<Id>::kPerLine;
@@ -936,6 +1018,86 @@ __device__ __forceinline__ void expand_split_body(const Sweep& c, Op& op) {
     if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count, c.qcap);
     op.flush();
 }
+#else
+template <class Op, class Id = uint64_t>
+__device__ __forceinline__ void expand_split_body(const Sweep& c, Op& op) {
+    constexpr int E = IdWidth<Id>::kPerStep, LINE = IdWidth<Id>::kPerLine;
+    // a step of 4-byte ids carries twice the ids: half the steps in flight
+    constexpr int KS = E == 4 && kSplitSteps >= EMOGI_IDS32_STEP_DIV ? kSplitSteps / EMOGI_IDS32_STEP_DIV
+                                                                      : kSplitSteps;
+    constexpr uint64_t STEP = 32 * E;  // ids per warp step
+    WarpQ wq = warpq_begin<Op>();
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long tot = *c.large;
+    const uint32_t nslots = (uint32_t)(tot >> SLOT_SHIFT);
+    const unsigned long long nitems = tot & CHUNK_MASK;
+    const unsigned long long per = (nitems + nwarps - 1) / nwarps;
+    unsigned long long item = warp * per;
+    const unsigned long long iend = item + per < nitems ? item + per : nitems;
+    const uint64_t item_ids = (uint64_t)LINE * c.chunk_lines;
+    if (item < iend) {  // warp-uniform
+        uint32_t lo = 0, hi = nslots;  // last slot whose first item <= item
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (c.lq_base[mid] <= item) lo = mid; else hi = mid;
+        }
+        uint32_t slot = lo, v = 0;
+        typename Op::S st = Op::kSkip;
+        uint64_t s = 0, e = 0, a = 0, pos = 0, ce = 0;
+        unsigned long long first = 0, slot_end = 0;
+        auto open_slot = [&]() {
+            v = c.lq_v[slot];
+            st = (typename Op::S)c.lq_state[slot];
+            s = c.off[v];
+            e = c.off[v + 1];
+            a = aligned_start<Id>(s, c.shift);
+            first = c.lq_base[slot];
+            slot_end = slot + 1 < nslots ? c.lq_base[slot + 1] : nitems;
+        };
+        auto open_item = [&]() {
+            pos = a + (item - first) * item_ids;
+            ce = pos + item_ids < e ? pos + item_ids : e;
+        };
+        open_slot();
+        open_item();
+        bool more = true;
+        while (more) {
+            typename StepOf<Id>::T p[KS];
+            typename CurOf<Id>::T cur[KS];
+            uint32_t vs[KS];
+            typename Op::S sts[KS];
+#pragma unroll
+            for (int u = 0; u < KS; u++) {
+                vs[u] = v;
+                sts[u] = st;
+                p[u] = load_step<Op, Id>(c, pos + E * lane, s, ce, more);
+                if (more) {
+                    pos += STEP;
+                    if (pos >= ce) {  // next item, and next list when the item was its last
+                        if (++item >= iend) {
+                            more = false;
+                        } else {
+                            if (item >= slot_end) {
+                                slot++;
+                                open_slot();
+                            }
+                            open_item();
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < KS; u++) cur[u] = peek_step(op, p[u]);
+#pragma unroll
+            for (int u = 0; u < KS; u++) visit_step(c, op, sts[u], vs[u], p[u], cur[u], wq);
+        }
+    }
+    if (Op::kPush) warpq_flush(wq, c.out_q, c.out_count, c.qcap);
+    op.flush();
+}
+#endif
 
 template <class Op, class Id = uint64_t>
 __global__ void __launch_bounds__(256) k_expand_split(Sweep c, Op op_in) {
@@ -1060,7 +1222,7 @@ __global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op_in) {
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t k = c.in_q ? (uint64_t)*c.in_count : (uint64_t)c.all_n;
-    unsigned long long scanned = 0;
+    unsigned long long scanned = 0, scanned_h = 0;
     for (uint64_t idx = warp; idx < k; idx += nwarps) {
         const uint32_t v = c.in_q ? c.in_q[idx] : (uint32_t)idx;
         typename Op::S st = Op::kSkip;
@@ -1077,7 +1239,7 @@ __global__ void __launch_bounds__(256) k_expand_merged(Sweep c, Op op_in) {
         }
     }
     __syncwarp();
-    add_scanned(c, scanned);
+    add_scanned(c, scanned, scanned_h);
     op.flush();
 }
 
@@ -1088,7 +1250,7 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
     const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const uint64_t nt = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t k = c.in_q ? (uint64_t)*c.in_count : (uint64_t)c.all_n;
-    unsigned long long scanned = 0;
+    unsigned long long scanned = 0, scanned_h = 0;
     for (uint64_t idx = tid; idx < k; idx += nt) {
         const uint32_t v = c.in_q ? c.in_q[idx] : (uint32_t)idx;
         const typename Op::S st = op.begin(v);
@@ -1103,7 +1265,7 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
         }
     }
     __syncwarp();
-    add_scanned(c, scanned);
+    add_scanned(c, scanned, scanned_h);
     op.flush();
 }
 
@@ -1455,7 +1617,7 @@ __global__ void __launch_bounds__(256) k_pr_pull(Sweep c, const double* contrib,
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t n = c.all_n;
-    unsigned long long scanned = 0;
+    unsigned long long scanned = 0, scanned_h = 0;
     for (uint64_t base = warp * GPW; base < n; base += nwarps * GPW) {
         const uint64_t v = base + grp;
         uint64_t s = 0, e = 0;
@@ -1488,7 +1650,7 @@ __global__ void __launch_bounds__(256) k_pr_pull(Sweep c, const double* contrib,
         for (int o = G / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
         if (glane == 0 && v < n && !split) acc[v] = sum;
     }
-    add_scanned(c, scanned);
+    add_scanned(c, scanned, scanned_h);
 }
 
 // The split lists of k_pr_pull: one warp per item, its sum added into acc[v].
@@ -1729,7 +1891,7 @@ __global__ void __launch_bounds__(256) k_ms_bottom_up(Sweep c, const unsigned lo
     const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t n = c.all_n;
-    unsigned long long scanned = 0;
+    unsigned long long scanned = 0, scanned_h = 0;
     for (uint64_t base = warp * 32; base < n; base += nwarps * 32) {
         const uint64_t v = base + lane;
         uint64_t s = 0, e = 0;
@@ -1808,7 +1970,7 @@ __global__ void __launch_bounds__(256) k_ms_bottom_up(Sweep c, const unsigned lo
             }
         }
     }
-    add_scanned(c, scanned);
+    add_scanned(c, scanned, scanned_h);
 }
 
 struct MsSources {

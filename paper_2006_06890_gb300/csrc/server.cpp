@@ -103,7 +103,7 @@ using namespace emogi;
 namespace {
 
 void finish_request(emogi_server s, const std::shared_ptr<Request>& r, emogi_status st, uint32_t batch,
-                    uint64_t reached, Clock::time_point started) {
+                    uint64_t reached, uint64_t scanned, Clock::time_point started) {
     r->finished = Clock::now();
     r->res.status = st;
     r->res.batch_size = batch;
@@ -111,6 +111,7 @@ void finish_request(emogi_server s, const std::shared_ptr<Request>& r, emogi_sta
     r->res.run_ms = ms_between(started, r->finished);
     r->res.latency_ms = ms_between(r->submitted, r->finished);
     r->res.edges_reached = reached;
+    r->res.edges_scanned = scanned;
     (void)s;
 }
 
@@ -131,7 +132,7 @@ void run_job(emogi_server s, Slot& slot, Job& job) {
     }
     const uint64_t n = job.g->n;
     const uint32_t k = (uint32_t)job.reqs.size();
-    std::vector<uint64_t> reached(k, 0);
+    std::vector<uint64_t> reached(k, 0), scanned(k, 0);
     emogi_opts o;
     memset(&o, 0, sizeof o);
     o.struct_size = sizeof o;
@@ -159,7 +160,10 @@ void run_job(emogi_server s, Slot& slot, Job& job) {
             if (st == EMOGI_OK && cudaStreamSynchronize(view->stream) != cudaSuccess)
                 st = fail(EMOGI_E_CUDA, "result copy failed");
             // per-source reached edges are not split out by the pass; report the batch total
-            for (uint32_t i = 0; i < k; i++) reached[i] = stt.edges_reached / k;
+            for (uint32_t i = 0; i < k; i++) {
+                reached[i] = stt.edges_reached / k;
+                scanned[i] = stt.edges_scanned / k;
+            }
         }
     } else if (st == EMOGI_OK) {
         for (uint32_t i = 0; i < k && st == EMOGI_OK; i++) {
@@ -182,13 +186,16 @@ void run_job(emogi_server s, Slot& slot, Job& job) {
             emogi_stats stt;
             st = job.kind == EMOGI_QUERY_SSSP ? emogi_sssp(view, r.src, out, &o, &stt)
                                               : emogi_bfs(view, r.src, out, &o, &stt);
-            if (st == EMOGI_OK) reached[i] = stt.edges_reached;
+            if (st == EMOGI_OK) {
+                reached[i] = stt.edges_reached;
+                scanned[i] = stt.edges_scanned;
+            }
         }
     }
     if (st != EMOGI_OK) err = emogi_last_error();
     std::lock_guard<std::mutex> lk(s->mu);
     for (uint32_t i = 0; i < k; i++) {
-        finish_request(s, job.reqs[i], st, k, reached[i], t0);
+        finish_request(s, job.reqs[i], st, k, reached[i], scanned[i], t0);
         job.reqs[i]->started = t0;
         job.reqs[i]->done = true;
     }
@@ -302,7 +309,7 @@ void scheduler_main(emogi_server s) {
         if (B && s->bytes_in_use + need() > B) {
             if (s->in_flight == 0) {  // nothing will free memory: this job can never fit
                 for (auto& r : job->reqs) {
-                    finish_request(s, r, EMOGI_E_BUDGET, k, 0, Clock::now());
+                    finish_request(s, r, EMOGI_E_BUDGET, k, 0, 0, Clock::now());
                     r->done = true;
                 }
                 s->cv_done.notify_all();

@@ -74,6 +74,8 @@ uint32_t auto_granularity(double avg_degree, uint32_t id_bytes) {
 #ifndef EMOGI_SSSP_TAIL_SHIFT
 #define EMOGI_SSSP_TAIL_SHIFT 12
 #endif
+static_assert(emogi::kShortMax == dev::kShortMax, "one bound for the short-list store");
+
 uint64_t sssp_tail(emogi_graph g) {
     if (!EMOGI_SSSP_TAIL_SHIFT || g->max_degree > dev::kHeavyEntries) return 0;
     return std::max<uint64_t>(g->n >> EMOGI_SSSP_TAIL_SHIFT, 256);
@@ -127,6 +129,10 @@ Sweep make_sweep(const Ctx& c, int side, bool all_vertices) {
     s.chunk_lines = c.chunk;
     s.scanned = &ws.ctr->scanned;
     s.heads = g->d_heads;
+    s.short_off = g->d_short_off;
+    s.short_ids = g->d_short_ids;
+    s.short_w = g->d_short_w;
+    s.scanned_heads = &ws.ctr->scanned_heads;
     s.m = g->m;
     s.qcap = (uint32_t)g->n;
     return s;
@@ -279,10 +285,10 @@ emogi_status read_counters(Ctx& c, bool after_sweep = true) {
         EMOGI_CUDA_TRY(cudaEventElapsedTime(&ms, ws.ev[2], ws.ev[3]));
         c.expand_ms += ms;
         if (trace_enabled())
-            fprintf(stderr, "[emogi] sweep %llu in=%u/%u out=%u/%u far=%u/%u scanned=%llu ms=%.4f\n",
+            fprintf(stderr, "[emogi] sweep %llu in=%u/%u out=%u/%u far=%u/%u scanned=%llu stored=%llu ms=%.4f\n",
                     (unsigned long long)c.expand_launches, ws.h_ctr->qcount[0], ws.h_ctr->qcount[1],
                     ws.h_ctr->qcount[1], ws.h_ctr->qcount[0], ws.h_ctr->fcount[0], ws.h_ctr->fcount[1],
-                    (unsigned long long)ws.h_ctr->scanned, ms);
+                    (unsigned long long)ws.h_ctr->scanned, (unsigned long long)ws.h_ctr->scanned_heads, ms);
     }
     return EMOGI_OK;
 }
@@ -317,8 +323,8 @@ emogi_status finish(Ctx& c, uint32_t* state, uint32_t* out, bool count_reached, 
         stats->iterations = iterations;
         stats->edges_scanned = ws.h_ctr->scanned;
         stats->edges_reached = count_reached ? ws.h_ctr->reached : g->m;
-        stats->edge_bytes = ws.h_ctr->scanned * g->id_bytes;
-        stats->weight_bytes = weights ? ws.h_ctr->scanned * 4ull : 0;
+        stats->edge_bytes = (ws.h_ctr->scanned - ws.h_ctr->scanned_heads) * g->id_bytes;
+        stats->weight_bytes = weights ? (ws.h_ctr->scanned - ws.h_ctr->scanned_heads) * 4ull : 0;
         stats->ms = ms;
         stats->expand_ms = c.expand_ms;
         stats->expand_launches = c.expand_launches;
@@ -779,7 +785,7 @@ emogi_status emogi_msbfs(emogi_graph g, const uint64_t* srcs, uint32_t k, uint32
         stats->iterations = it;
         stats->edges_scanned = ws.h_ctr->scanned;
         stats->edges_reached = ws.h_ctr->reached;
-        stats->edge_bytes = ws.h_ctr->scanned * g->id_bytes;
+        stats->edge_bytes = (ws.h_ctr->scanned - ws.h_ctr->scanned_heads) * g->id_bytes;
         stats->ms = ms;
         stats->expand_ms = c.expand_ms;
         stats->expand_launches = c.expand_launches;
@@ -804,7 +810,7 @@ emogi_status emogi_pagerank(emogi_graph g, double damping, double tolerance, uin
         EMOGI_TRY(dev_alloc((void**)&ws.pr_acc, n * 8, "PageRank sums"));
         EMOGI_TRY(dev_alloc(&ws.pr_ctr, 64, "PageRank counters"));
         EMOGI_CUDA_TRY(cudaHostAlloc(&ws.h_pr_ctr, 64, cudaHostAllocDefault));
-        EMOGI_CUDA_TRY(cudaMemset(ws.pr_acc, 0, n * 8));
+        EMOGI_CUDA_TRY(cudaMemsetAsync(ws.pr_acc, 0, n * 8, c.st));  // on the call's stream, before its kernels
     }
     double* r = rank;
     if (!c.o.out_on_device) {
@@ -879,7 +885,7 @@ emogi_status emogi_pagerank(emogi_graph g, double damping, double tolerance, uin
         stats->iterations = it;
         stats->edges_scanned = ws.h_ctr->scanned;
         stats->edges_reached = g->m * (uint64_t)it;
-        stats->edge_bytes = ws.h_ctr->scanned * g->id_bytes;
+        stats->edge_bytes = (ws.h_ctr->scanned - ws.h_ctr->scanned_heads) * g->id_bytes;
         stats->ms = ms;
         stats->expand_ms = c.expand_ms;
         stats->expand_launches = c.expand_launches;

@@ -82,6 +82,8 @@ _SIGNATURES = [
     ("emogi_msbfs", _I32, [_P, _P, _U32, _P, ctypes.POINTER(Opts), ctypes.POINTER(Stats)]),
     ("emogi_set_device_budget", _I32, [_U64]),
     ("emogi_device_bytes_in_use", _U64, []),
+    ("emogi_managed_alloc", _I32, [_U64, ctypes.POINTER(_P)]),
+    ("emogi_managed_free", _I32, [_P]),
     ("emogi_free_graph", _I32, [_P]),
     ("emogi_graph_num_vertices", _U64, [_P]),
     ("emogi_graph_num_edges", _U64, [_P]),
@@ -158,6 +160,20 @@ def set_device_budget(nbytes: int):
 
 def device_bytes_in_use() -> int:
     return int(lib().emogi_device_bytes_in_use())
+
+
+def managed_empty(count: int, dtype) -> np.ndarray:
+    """An uninitialised numpy array over managed (UVM) memory from
+    emogi_managed_alloc, for load_csr(..., placement="managed", borrow=True).
+    The memory is freed once the array and every view of it are gone."""
+    import weakref
+    dtype = np.dtype(dtype)
+    nbytes = max(1, int(count)) * dtype.itemsize
+    p = ctypes.c_void_p()
+    _check(lib().emogi_managed_alloc(nbytes, ctypes.byref(p)))
+    buf = (ctypes.c_uint8 * nbytes).from_address(p.value)
+    weakref.finalize(buf, lib().emogi_managed_free, ctypes.c_void_p(p.value))
+    return np.frombuffer(buf, dtype=np.uint8).view(dtype)[:int(count)]
 
 
 def test_fail_device_alloc_after(k: int):
@@ -468,7 +484,7 @@ class ServerConfig(ctypes.Structure):
 class QueryResult(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("batch_size", ctypes.c_uint32), ("queue_ms", ctypes.c_double),
                 ("run_ms", ctypes.c_double), ("latency_ms", ctypes.c_double),
-                ("edges_reached", ctypes.c_uint64)]
+                ("edges_reached", ctypes.c_uint64), ("edges_scanned", ctypes.c_uint64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

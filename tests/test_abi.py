@@ -78,7 +78,7 @@ def test_load32_rejects_bad_csr_on_host(E):
     assert e.status == E.E_ARG and "decrease" in str(e)
     e = bad(3, 2, np.array([0, 1, 2, 2], dtype=u), np.array([1, 3], dtype=u32))
     assert e.status == E.E_ARG and "col_idx[1] = 3" in str(e)
-    e = bad(2, 2, np.array([0, 1, 2], dtype=u), np.array([1, 0], dtype=u32), placement="managed", borrow=True)
+    e = bad(2, 2, np.array([0, 1, 2], dtype=u), np.array([1, 0], dtype=u32), placement="device", borrow=True)
     assert e.status == E.E_ARG and "BORROW" in str(e)
 
 

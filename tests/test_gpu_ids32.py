@@ -91,13 +91,18 @@ def test_ids32_borrowed_arrays_at_every_16_byte_offset():
 def test_ids32_stats_count_four_bytes_per_id():
     g = graph("kron16")
     s = gg.max_degree_vertex(g)
-    with load32(g, placement="host") as h:
+    deg = g.degrees()
+    with load32(g, placement="host", heads=False) as h:  # every entry from the edge list
         lv, st = E.bfs(h, s, top_down_only=True)
         reached = oracle.reached_edges(g.offsets, lv)
         assert st["edges_scanned"] == reached
         assert st["edge_bytes"] == 4 * reached
         _, st = E.sssp(h, s)
         assert st["edge_bytes"] == 4 * st["edges_scanned"] and st["weight_bytes"] == 4 * st["edges_scanned"]
+    with load32(g, placement="host") as h:  # lists of at most 16 entries from the short-list store
+        lv, st = E.bfs(h, s, top_down_only=True)
+        short = int(deg[(lv != E.INF) & (deg <= 16)].sum())
+        assert st["edge_bytes"] == 4 * (oracle.reached_edges(g.offsets, lv) - short)
 
 
 @pytest.mark.parametrize("name", ["kron16", "urand14", "hub", "path", "directed"])

@@ -391,11 +391,14 @@ def test_direction_optimising_reads_less_on_dense_levels():
 def test_stats_are_consistent():
     g = graph("kron16")
     s = gg.max_degree_vertex(g)
+    deg = g.degrees()
     with E.load_graph(g, placement="host") as h:
         lv, st = E.bfs(h, s, time_kernels=True, top_down_only=True)
         reached = oracle.reached_edges(g.offsets, lv)
         assert st["edges_scanned"] == reached  # BFS expands each reached vertex once
-        assert st["edge_bytes"] == 8 * reached
+        # lists of at most 16 entries come from the short-list store in GPU memory
+        short = int(deg[(lv != E.INF) & (deg <= 16)].sum())
+        assert st["edge_bytes"] == 8 * (reached - short)
         assert st["iterations"] == int(lv[lv != E.INF].max()) + 1
         assert st["expand_launches"] == st["iterations"]
         assert 0 < st["expand_ms"] <= st["ms"]
@@ -634,3 +637,67 @@ def test_host_arrays_of_a_gib_or_more():
             np.testing.assert_array_equal(E.bfs(h, s)[0], exp_bfs)
             np.testing.assert_array_equal(E.sssp(h, s)[0], exp_sssp)
             np.testing.assert_array_equal(E.cc(h)[0], exp_cc)
+
+
+def test_borrowed_managed_arrays():
+    """EMOGI_PLACE_MANAGED | EMOGI_LOAD_BORROW reads the caller's managed
+    arrays in place (read-mostly advice); results equal the oracle's, a
+    managed list starting 16 bytes past a line included, and plain host
+    memory is rejected."""
+    g = graph("kron12")
+    for shift in (0, 2):
+        cols = E.managed_empty(g.m + 16, np.uint64)[shift:shift + g.m]
+        cols[:] = g.cols
+        w = E.managed_empty(g.m + 32, np.uint32)[2 * shift:2 * shift + g.m]
+        w[:] = g.weights
+        with E.load_csr(g.n, g.m, g.offsets, cols, w, placement="managed", borrow=True, undirected=True) as h:
+            check_all(g, h)
+        del cols, w
+    with pytest.raises(E.EmogiError) as ei:
+        E.load_csr(g.n, g.m, g.offsets, g.cols, g.weights, placement="managed", borrow=True, undirected=True)
+    assert ei.value.status == E.E_ARG and "cudaMallocManaged" in str(ei.value)
+
+
+def short_lists_graph(n=20000):
+    """Lists of 0 to 19 entries (those of at most 16 are read whole from the
+    short-list store in GPU memory, the others from the edge list), every
+    multiplicity and order, with a few long lists among them, weights in
+    [1, 255]."""
+    rng = np.random.default_rng(12)
+    deg = rng.integers(0, 20, size=n)
+    deg[rng.integers(0, n, size=40)] = rng.integers(5, 700, size=40)
+    src = np.repeat(np.arange(n), deg)
+    dst = rng.integers(0, n, size=src.size)
+    return gg.csr_from_edges(n, src, dst, weights=rng.integers(1, 256, size=src.size), symmetrize=False,
+                             dedup=False, drop_self_loops=False, sort=False, name="short-lists")
+
+
+@pytest.mark.parametrize("placement", ["host", "managed"])
+@pytest.mark.parametrize("ids32", [False, True], ids=["u64", "u32"])
+def test_short_lists_from_heads_sssp_bfs(placement, ids32):
+    """Lists of at most sixteen entries come from the short-list store in GPU
+    memory (ids, and weights for SSSP); results equal the oracle's with the
+    store on and off, and the bytes reported as read from the edge list leave
+    out the entries the store served."""
+    g = short_lists_graph()
+    g.undirected = False
+    srcs = [int(s) for s in gg.random_sources(g, 3, seed=4)] + [gg.max_degree_vertex(g)]
+    deg = g.degrees()
+    for heads in (True, False):
+        with E.load_graph(g, placement=placement, heads=heads, ids32=ids32) as h:
+            for s in srcs:
+                exp_d = oracle.sssp_g(g, s)
+                for kw in (dict(), dict(host_loop=True), dict(granularity=4), dict(ordered_frontier=True)):
+                    d, st = E.sssp(h, s, **kw)
+                    np.testing.assert_array_equal(d, exp_d, err_msg=f"heads={heads} src={s} {kw}")
+                    assert st["edge_bytes"] <= st["edges_scanned"] * (4 if ids32 else 8)
+                    if not heads:
+                        assert st["edge_bytes"] == st["edges_scanned"] * (4 if ids32 else 8)
+                        assert st["weight_bytes"] == st["edges_scanned"] * 4
+                lv, st = E.bfs(h, s, top_down_only=True)
+                exp = oracle.bfs_g(g, s)
+                np.testing.assert_array_equal(lv, exp, err_msg=f"heads={heads} src={s}")
+                if heads:  # every reached list of <= 16 entries came from the store
+                    short = int(deg[(exp != E.INF) & (deg <= 16)].sum())
+                    assert st["edges_scanned"] * (4 if ids32 else 8) - st["edge_bytes"] == \
+                        short * (4 if ids32 else 8)
