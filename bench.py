@@ -260,20 +260,14 @@ def step_alg_bytes(stats):
     return sum(link_bytes(s) for s in stats)
 
 
-# Host-link read bytes per algorithmic byte of the expansion kernels, from the
-# ncu sysmem read-sector counts of the same kernels on a smaller graph of the
-# same family (uniform: 2^22 vertices, profiles/link_traffic_per_kernel_
-# urand22_host.md; Kronecker: scale 23, profiles/link_traffic_per_kernel_
-# kron23_host.md); the 32-byte sector waste of lists that do not start on a
-# sector grows with the entries read, so the per-entry factor scales to the
-# full graph.  None = not measured for the current kernels.
-LINK_BYTES_PER_ALG_BYTE = {"urand": {"bfs": 1.130, "sssp": 1.135, "cc": 1.0},
-                           "kron": None}
-
-
-def step_link_bytes(stats, factors):
-    sb, ss, sc = stats
-    return factors["bfs"] * link_bytes(sb) + factors["sssp"] * link_bytes(ss) + factors["cc"] * link_bytes(sc)
+# Host-link read bytes per algorithmic byte of the SSSP sweeps, from ncu's
+# sysmem read-sector counts of the same kernels on a smaller graph of the same
+# family (uniform: 2^22 vertices, profiles/link_traffic_per_kernel_urand22_host.md;
+# Kronecker: scale 23, edge factor 32, profiles/link_traffic_sssp_kron23_host.md).
+# The 32-byte sector waste of lists that do not start on a sector grows with
+# the entries read, so the per-byte factor scales to the full graph; on the
+# Kronecker graph most entries sit in long lists and the waste is about 1 %.
+LINK_BYTES_PER_ALG_BYTE = {"urand": {"sssp": 1.135}, "kron": {"sssp": 1.011}}
 
 
 def combine_over_ranks(ms, units, world, device="cuda"):
@@ -522,6 +516,7 @@ def ours(args):
     if args.workload == "kron27":
         g, srcs, ginfo = make_kron27()
         ginfo["huge_pages"] = gg.huge_page_report()
+        ginfo["numa"] = gg.numa_report(g.cols, g.weights)
     else:
         g, srcs = make_urand24()
         ginfo = {}
@@ -827,9 +822,13 @@ def extra_serving(E, torch):
         def link_bytes(gi, kind, scanned):
             return scanned * (12 if kind == "sssp" else 8) if places[gi] == "host" else 0
 
-        def summarise(qs, lat, runs, scanned, wall, slots=1):
+        def summarise(qs, lat, runs, scanned, wall, slots=1, batch=None):
+            """runs: each query's job time; a job of b queries reports its time on
+            each of them, so slot time counts runs / b per query (each job once)."""
             lat = np.asarray(lat)
             kinds = np.array([k for _, k, _ in qs])
+            nb = np.asarray(batch, dtype=np.float64) if batch is not None else np.ones(len(qs))
+            runs = np.asarray(runs, dtype=np.float64) / nb
             r = {"queries": len(qs), "queries_per_s": round(len(qs) / wall, 1),
                  "p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
                  "link_gbs": round(sum(link_bytes(gi, k, sc) for (gi, k, _), sc in zip(qs, scanned)) / wall / 1e9, 2)}
@@ -838,9 +837,15 @@ def extra_serving(E, torch):
                 if sel.any():
                     r[kind] = {"p50_ms": round(float(np.percentile(lat[sel], 50)), 3),
                                "p99_ms": round(float(np.percentile(lat[sel], 99)), 3),
-                               "slot_time_share": round(float(np.sum(np.asarray(runs)[sel])) /
-                                                        max(float(np.sum(runs)), 1e-9), 3)}
+                               "slot_time_share": round(float(np.sum(runs[sel])) / max(float(np.sum(runs)), 1e-9), 3),
+                               "job_ms_mean": round(float(np.sum(runs[sel])) / max(float(np.sum(1.0 / nb[sel])), 1e-9),
+                                                    3)}
             r["slot_busy"] = round(float(np.sum(runs)) / 1e3 / (wall * slots), 3)
+            by = {}
+            for (gi, kind, _), t in zip(qs, runs):
+                d = by.setdefault(specs[gi][0], {"bfs": 0.0, "sssp": 0.0})
+                d[kind] += t / 1e3
+            r["slot_s_by_graph"] = {k: {kk: round(vv, 2) for kk, vv in v.items()} for k, v in by.items()}
             return r
 
         # one query at a time through the plain calls
@@ -878,7 +883,7 @@ def extra_serving(E, torch):
                 res = [srv.wait(t) for t in tickets]
                 wall = time.perf_counter() - tl
                 r = summarise(qs, [x["latency_ms"] for x in res], [x["run_ms"] for x in res],
-                              [x["edges_scanned"] for x in res], wall, slots)
+                              [x["edges_scanned"] for x in res], wall, slots, [x["batch_size"] for x in res])
                 r["offered_qps"] = rate
                 r["mean_batch"] = round(float(np.mean([x["batch_size"] for x in res])), 2)
                 r["max_batch"] = int(max(x["batch_size"] for x in res))

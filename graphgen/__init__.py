@@ -118,6 +118,39 @@ def huge_page_report() -> dict:
     return out
 
 
+def numa_report(*arrays) -> dict:
+    """Where the host pages of the given arrays live: for each array, the NUMA
+    nodes holding its mapping's pages and the mapping's page size (from
+    /proc/self/numa_maps), and the kernel's automatic NUMA balancing setting
+    (which unmaps pages now and then to sample accesses)."""
+    out = {}
+    try:
+        with open("/proc/sys/kernel/numa_balancing") as f:
+            out["numa_balancing"] = f.read().strip()
+    except OSError:
+        out["numa_balancing"] = None
+    try:
+        maps = []
+        with open("/proc/self/numa_maps") as f:
+            for line in f:
+                parts = line.split()
+                maps.append((int(parts[0], 16), parts[1:]))
+        maps.sort()
+        for i, a in enumerate(arrays):
+            addr, best = a.ctypes.data, None
+            for start, fields in maps:
+                if start > addr:
+                    break
+                best = fields
+            if best is not None:
+                rec = dict(f.split("=", 1) for f in best if "=" in f)
+                out[f"array{i}"] = {k: v for k, v in rec.items()
+                                    if k.startswith("N") or k in ("kernelpagesize_kB", "anon")}
+    except (OSError, ValueError):
+        pass
+    return out
+
+
 def release_host_range(arr: np.ndarray, lo: int, hi: int) -> int:
     """Return the physical pages wholly inside elements [lo, hi) of a 1-D
     array to the operating system (madvise MADV_DONTNEED; for anonymous
