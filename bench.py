@@ -545,6 +545,7 @@ def ours(args):
     else:
         h = E.load_graph(g, placement="host")
         factors = LINK_BYTES_PER_ALG_BYTE["urand"]
+    ginfo["store_bound"] = h.store_bound  # lists of 1..store_bound entries are read from GPU memory
     link_peak = pinned_h2d_peak_gbs(torch)
 
     hl = headline(torch, E, h, g, srcs, stream, args, world, barrier)

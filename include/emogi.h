@@ -62,11 +62,12 @@ enum {
     EMOGI_LOAD_UNDIRECTED = 1u << 0, /* caller asserts the CSR is symmetric; required by emogi_cc */
     EMOGI_LOAD_BORROW = 1u << 1,     /* HOST: pin and map the caller's arrays in place, no copy;
                                         MANAGED: use the caller's managed arrays in place */
-    EMOGI_LOAD_NO_HEADS = 1u << 2    /* HOST / MANAGED: do not mirror the first 4 ids of every list (and,
-                                        with weights, their weights) in GPU memory (16 bytes per vertex,
-                                        32 with weights; sampled CC and bottom-up BFS read them there, and
-                                        lists of at most 4 entries are read from there whole, instead of
-                                        over the host link) */
+    EMOGI_LOAD_NO_HEADS = 1u << 2    /* HOST / MANAGED: mirror nothing of the edge list in GPU memory:
+                                        neither the first 4 ids of every list (16 bytes per vertex, read
+                                        by sampled CC and bottom-up BFS) nor the short-list store (every
+                                        list of at most 16 or 32 entries, ids and weights, see
+                                        emogi_graph_store_bound); every list entry is then read over
+                                        the host link */
 };
 
 /* How a worker reads one neighbour list (Sec. 4.2, Sec. 4.3, Listings
@@ -393,6 +394,18 @@ uint64_t emogi_graph_workspace_bytes(emogi_graph g);
 uint64_t emogi_graph_num_vertices(emogi_graph g);
 uint64_t emogi_graph_num_edges(emogi_graph g);
 int emogi_graph_placement(emogi_graph g);
+
+/* The longest list held by the graph's short-list store in GPU memory: the
+ * traversals read every list of 1..this many entries there (ids, and weights
+ * when loaded), not from the edge list, and leave those entries out of
+ * emogi_stats.edge_bytes / weight_bytes.  32 when the lists of up to 32
+ * entries hold at most 1/8 of the graph's entries (degree-skewed graphs),
+ * else 16; 0 when there is no store: DEVICE placement, EMOGI_LOAD_NO_HEADS,
+ * or no room for it in the device budget next to one handle's work buffers
+ * (a store that does not fit is left out rather than failing the load).
+ * This is a GB300-side cache with no counterpart in the paper, whose edge
+ * list is read only over the link. */
+uint32_t emogi_graph_store_bound(emogi_graph g);
 
 /* Static description of a status code. */
 const char* emogi_status_string(emogi_status s);

@@ -112,16 +112,23 @@ emogi_status parse_opts(const emogi_opts* in, Opts* o) {
 }
 
 // ---------------------------------------------------------------- work buffers
+// split-list vertices: a list is split when its aligned span exceeds 32 lines
+// (512 uint64 ids or 1024 uint32 ids); the span starts at most 15 (31) ids
+// before the list, so a split list holds at least 498 ids and one sweep splits
+// at most m / 498
+static uint64_t split_cap(uint64_t n, uint64_t m) { return std::min<uint64_t>(n, m / 497 + 1); }
+
+uint64_t workspace_need(uint64_t n, uint64_t m) {
+    n = n ? n : 1;
+    return 6 * n * 4 + (n / 16 + 1) * 16 + split_cap(n, m) * 20 + sizeof(DevCounters) + 256;  // + SSSP loop state
+}
+
 emogi_status ensure_workspace(emogi_graph g) {
     Workspace& ws = g->ws;
     if (ws.ctr) return EMOGI_OK;
     const uint64_t n = g->n ? g->n : 1;
     ws.n = n;
-    // split-list vertices: a list is split when its aligned span exceeds 32
-    // lines (512 uint64 ids or 1024 uint32 ids); the span starts at most 15
-    // (31) ids before the list, so a split list holds at least 498 ids and
-    // one sweep splits at most m / 498
-    ws.lq_cap = std::min<uint64_t>(n, g->m / 497 + 1);
+    ws.lq_cap = split_cap(n, g->m);
     struct Item { void** p; size_t bytes; const char* what; };
     Item items[] = {
         {(void**)&ws.q[0], n * 4, "frontier queue 0"},
@@ -427,37 +434,75 @@ static emogi_status build_heads(emogi_graph g, const uint64_t* off, const Id* co
     return EMOGI_OK;
 }
 
-// The short-list store: every list of 1..kShortMax entries, copied whole
+// The short-list store: every list of 1..g->short_max entries, copied whole
 // (ids, and weights when given) into GPU memory, lists starting on 4-entry
 // boundaries; short_off[v] is the start in units of 4 entries (lists longer
-// than kShortMax or empty get 0 and are never read there).  Built on the host
-// from the caller's arrays in two parallel passes (slot counts per block of
-// vertices, then the copy), then copied to the device.
+// than that or empty get 0 and are never read there).  The bound is
+// kStoreWide when the lists up to that length hold at most 1/kStoreShare of
+// the entries, else kStoreBase; a bound whose store (with the index) and the
+// work buffers of one handle do not fit what the device budget leaves is
+// dropped for the smaller one, and then for no store.  Built on the host from
+// the caller's arrays in two parallel passes (counts per block of vertices
+// for both bounds, then the copy), then copied to the device.
 template <class Id>
 static emogi_status build_short_store(emogi_graph g, const uint64_t* off, const Id* cols, const uint32_t* weights) {
     const uint64_t n = g->n;
     unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
     if (n < 65536) nt = 1;
-    auto slots_of = [&](uint64_t v) -> uint64_t {
+    auto slots_of = [&](uint64_t v, uint32_t bound) -> uint64_t {
         const uint64_t d = off[v + 1] - off[v];
-        return d >= 1 && d <= kShortMax ? (d + 3) / 4 * 4 : 0;
+        return d >= 1 && d <= bound ? (d + 3) / 4 * 4 : 0;
     };
-    std::vector<uint64_t> part(nt + 1, 0);
+    // per block of vertices: slots and entries of the lists of 1..kStoreBase
+    // and of 1..kStoreWide entries
+    struct Count { uint64_t slots[2] = {0, 0}, ents[2] = {0, 0}; };
+    std::vector<Count> cnt(nt);
     {
         std::vector<std::thread> th;
         auto count = [&](unsigned t) {
-            uint64_t x = 0;
-            for (uint64_t v = n * t / nt; v < n * (t + 1) / nt; v++) x += slots_of(v);
-            part[t + 1] = x;
+            Count x;
+            for (uint64_t v = n * t / nt; v < n * (t + 1) / nt; v++) {
+                const uint64_t d = off[v + 1] - off[v];
+                if (d < 1 || d > kStoreWide) continue;
+                const uint64_t k = (d + 3) / 4 * 4;
+                x.slots[1] += k;
+                x.ents[1] += d;
+                if (d <= kStoreBase) {
+                    x.slots[0] += k;
+                    x.ents[0] += d;
+                }
+            }
+            cnt[t] = x;
         };
         for (unsigned t = 1; t < nt; t++) th.emplace_back(count, t);
         count(0);
         for (auto& x : th) x.join();
     }
-    for (unsigned t = 0; t < nt; t++) part[t + 1] += part[t];
+    Count all;
+    for (const auto& x : cnt)
+        for (int b = 0; b < 2; b++) {
+            all.slots[b] += x.slots[b];
+            all.ents[b] += x.ents[b];
+        }
+    const uint64_t budget = g_budget.load();
+    auto fits = [&](int b) {
+        if (all.slots[b] == 0 || all.slots[b] / 4 >= 0xFFFFFFFFull) return false;  // the uint32 index
+        if (!budget) return true;
+        const uint64_t need = n * 4 + all.slots[b] * (weights ? 8 : 4) + workspace_need(n, g->m);
+        const uint64_t used = g_in_use.load();
+        return used <= budget && need <= budget - used;
+    };
+    int pick = -1;
+    if (all.ents[1] * kStoreShare <= g->m && fits(1)) pick = 1;
+    else if (fits(0)) pick = 0;
+    if (pick < 0) {  // nothing to store, or no room for it
+        g->short_max = 0;
+        return EMOGI_OK;
+    }
+    g->short_max = pick ? kStoreWide : kStoreBase;
+    std::vector<uint64_t> part(nt + 1, 0);
+    for (unsigned t = 0; t < nt; t++) part[t + 1] = part[t] + cnt[t].slots[pick];
     const uint64_t slots = part[nt];
-    if (slots == 0) return EMOGI_OK;
-    if (slots / 4 >= 0xFFFFFFFFull) return EMOGI_OK;  // the uint32 index cannot address it: no store
     std::vector<uint32_t> so, sid, sw;
     try {
         so.resize(n);
@@ -473,7 +518,7 @@ static emogi_status build_short_store(emogi_graph g, const uint64_t* off, const 
         auto fill = [&](unsigned t) {
             uint64_t pos = part[t], e = 0;
             for (uint64_t v = n * t / nt; v < n * (t + 1) / nt; v++) {
-                const uint64_t k = slots_of(v);
+                const uint64_t k = slots_of(v, g->short_max);
                 so[v] = (uint32_t)(pos / 4);
                 if (!k) continue;
                 const uint64_t d = off[v + 1] - off[v];
@@ -593,7 +638,7 @@ static emogi_status load_csr(uint64_t n, uint64_t m, const uint64_t* row_offsets
     }
     // list heads and the short-list store: when the edge list itself is not in
     // GPU memory, the first ids of every list (16 bytes per vertex) and every
-    // list of at most kShortMax entries (ids and weights) are mirrored there
+    // list of at most 16 or 32 entries (ids and weights) are mirrored there
     if (place != EMOGI_PLACE_DEVICE && !(flags & EMOGI_LOAD_NO_HEADS) && n && m) {
         s = dev_alloc((void**)&g->d_heads, n * 4 * sizeof(uint32_t), "list heads");
         if (s != EMOGI_OK) return bail(s);
@@ -716,6 +761,7 @@ emogi_status emogi_graph_share(emogi_graph g, emogi_graph* out) {
     h->d_short_off = g->d_short_off;
     h->d_short_ids = g->d_short_ids;
     h->d_short_w = g->d_short_w;
+    h->short_max = g->short_max;
     h->short_slots = g->short_slots;
     h->short_entries = g->short_entries;
     h->cols = g->cols;
@@ -741,5 +787,6 @@ uint64_t emogi_graph_workspace_bytes(emogi_graph g) { return g ? g->ws.dev_bytes
 uint64_t emogi_graph_num_vertices(emogi_graph g) { return g ? g->n : 0; }
 uint64_t emogi_graph_num_edges(emogi_graph g) { return g ? g->m : 0; }
 int emogi_graph_placement(emogi_graph g) { return g ? g->place : -1; }
+uint32_t emogi_graph_store_bound(emogi_graph g) { return g ? g->short_max : 0; }
 
 }  // extern "C"

@@ -11,10 +11,18 @@
 
 namespace emogi {
 
-// Lists of at most this many entries are mirrored whole in GPU memory (the
-// short-list store) when the edge list is not there; the kernels' copy of the
-// constant is checked against this one where both are visible.
-constexpr uint64_t kShortMax = 16;
+// The short-list store (whole lists mirrored in GPU memory when the edge list
+// is not there) holds every list of 1..kStoreBase entries, and of
+// 1..kStoreWide entries when those hold at most 1/kStoreShare of the graph's
+// entries: on degree-skewed graphs they are most of the vertices but few of
+// the edges (Kronecker graphs of edge factor 32: 4-8 %), while on a uniform
+// graph of mean degree 32 they are half of the edge list, which then stays
+// where the caller placed it.  Measured on GB300, Kronecker scale 27 SSSP from host memory:
+// 845 ms with a bound of 16 entries, 731 ms with 32 (1.0 GB more of GPU
+// memory); 64 and 128 read 5 % fewer link bytes for 3.4 GB more and ran
+// 666-1195 ms.  A bound whose store does not fit the device budget, with
+// room left for the work buffers, is not taken.
+constexpr uint32_t kStoreBase = 16, kStoreWide = 32, kStoreShare = 8;
 
 // ---------------------------------------------------------------- errors
 void set_error(const std::string& msg);
@@ -123,12 +131,13 @@ struct emogi_graph_s {
     int place = EMOGI_PLACE_DEVICE;
     uint64_t* d_off = nullptr;         // device row offsets (n + 1)
     uint32_t* d_heads = nullptr;       // first 4 ids of every list in GPU memory (edge lists off the GPU)
-    // short-list store: every list of 1..kShortMax entries copied whole to GPU
+    // short-list store: every list of 1..short_max entries copied whole to GPU
     // memory (ids as uint32, and weights), each starting on a 4-entry boundary;
     // d_short_off[v] = start of v's list in units of 4 entries (edge lists off the GPU)
     uint32_t* d_short_off = nullptr;
     uint32_t* d_short_ids = nullptr;
     uint32_t* d_short_w = nullptr;
+    uint32_t short_max = 0;            // longest list the store holds (0 = no store)
     uint64_t short_slots = 0;          // entries the store holds (padding included)
     uint64_t short_entries = 0;        // list entries it holds
     const void* cols = nullptr;        // kernel-visible edge list (uint64 or uint32 ids)
@@ -150,6 +159,7 @@ struct emogi_graph_s {
 
 namespace emogi {
 emogi_status ensure_workspace(emogi_graph g);
+uint64_t workspace_need(uint64_t n, uint64_t m);  // device bytes ensure_workspace allocates
 void release_workspace(emogi_graph g);
 int sm_count(int device);
 }  // namespace emogi

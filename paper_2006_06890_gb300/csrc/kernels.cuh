@@ -54,9 +54,10 @@ struct Sweep {
     uint32_t chunk_lines = 1;            // lines per split work item
     unsigned long long* scanned = nullptr;         // neighbour entries read (statistics)
     const uint32_t* heads = nullptr;     // first kHeads ids of every list in GPU memory, or null
-    const uint32_t* short_off = nullptr; // short-list store (see kShortMax): start of v's list / 4, or null
+    const uint32_t* short_off = nullptr; // short-list store: start of v's list / 4, or null
     const uint32_t* short_ids = nullptr;
     const uint32_t* short_w = nullptr;   // its weights (weighted graphs), or null
+    uint32_t short_max = 0;              // longest list the store holds
     unsigned long long* scanned_heads = nullptr;  // entries read from the store instead of the edge list
     uint64_t m = 0;                      // entries in the edge list (and weights): a lane's 16-byte
                                          // load at index j is whole when j + ids per load <= m
@@ -66,9 +67,7 @@ struct Sweep {
 
 // Entries of each list mirrored in GPU memory ("list heads", INF-padded).
 constexpr int kHeads = 4;
-// Lists of at most kShortMax entries are mirrored whole in GPU memory (the
-// short-list store) when the edge list is not there.
-constexpr uint32_t kShortMax = 16;
+
 
 // ------------------------------------------------------------------ loads
 // Edge-list reads go through the non-coherent read-only path and do not
@@ -639,7 +638,7 @@ __device__ __forceinline__ typename StepOf<Id>::T load_step(const Sweep& c, uint
     else return load_quad<Op>(c, j, s, e, active);
 }
 
-// Whole lists of at most kShortMax entries are read from the short-list store
+// Whole lists of at most short_max entries are read from the short-list store
 // in GPU memory (ids, and weights when the op reads them) instead of the edge
 // list, in the same steps a list read makes, so peek and visit are unchanged.
 // Where an edge list sits in host memory, a sweep over a sparse frontier (a
@@ -652,7 +651,7 @@ __device__ __forceinline__ typename StepOf<Id>::T load_step(const Sweep& c, uint
 // lane's two or four entries are one 8- or 16-byte load.
 template <class Op>
 __device__ __forceinline__ bool reads_store(const Sweep& c, uint64_t s, uint64_t e) {
-    return c.short_off && (!Op::kWeights || c.short_w) && e > s && e - s <= (uint64_t)kShortMax;
+    return c.short_off && (!Op::kWeights || c.short_w) && e > s && e - s <= (uint64_t)c.short_max;
 }
 template <class Op, class Id>
 __device__ __forceinline__ typename StepOf<Id>::T store_step(const Sweep& c, uint32_t v, uint32_t j, uint32_t len,

@@ -74,8 +74,6 @@ uint32_t auto_granularity(double avg_degree, uint32_t id_bytes) {
 #ifndef EMOGI_SSSP_TAIL_SHIFT
 #define EMOGI_SSSP_TAIL_SHIFT 12
 #endif
-static_assert(emogi::kShortMax == dev::kShortMax, "one bound for the short-list store");
-
 uint64_t sssp_tail(emogi_graph g) {
     if (!EMOGI_SSSP_TAIL_SHIFT || g->max_degree > dev::kHeavyEntries) return 0;
     return std::max<uint64_t>(g->n >> EMOGI_SSSP_TAIL_SHIFT, 256);
@@ -132,6 +130,7 @@ Sweep make_sweep(const Ctx& c, int side, bool all_vertices) {
     s.short_off = g->d_short_off;
     s.short_ids = g->d_short_ids;
     s.short_w = g->d_short_w;
+    s.short_max = g->short_max;
     s.scanned_heads = &ws.ctr->scanned_heads;
     s.m = g->m;
     s.qcap = (uint32_t)g->n;

@@ -88,6 +88,7 @@ _SIGNATURES = [
     ("emogi_graph_num_vertices", _U64, [_P]),
     ("emogi_graph_num_edges", _U64, [_P]),
     ("emogi_graph_placement", _I32, [_P]),
+    ("emogi_graph_store_bound", _U32, [_P]),
     ("emogi_graph_share", _I32, [_P, ctypes.POINTER(_P)]),
     ("emogi_graph_workspace_bytes", _U64, [_P]),
     ("emogi_status_string", ctypes.c_char_p, [_I32]),
@@ -217,6 +218,11 @@ class Graph:
 
     def workspace_bytes(self) -> int:
         return int(lib().emogi_graph_workspace_bytes(self.handle))
+
+    @property
+    def store_bound(self) -> int:
+        """Lists of 1..store_bound entries are read from the short-list store in GPU memory (0: no store)."""
+        return int(lib().emogi_graph_store_bound(self.handle))
 
     def __enter__(self):
         return self

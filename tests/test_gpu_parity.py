@@ -388,6 +388,68 @@ def test_direction_optimising_reads_less_on_dense_levels():
         assert do["edges_scanned"] < 0.5 * td["edges_scanned"]
 
 
+def store_skew_graph(n=4000):
+    """Most lists hold 1 to 32 entries, ten hubs hold about 94 % of the
+    entries (lists of 80k to 120k entries, split across warps): the
+    short-list store takes lists of up to 32 entries."""
+    rng = np.random.default_rng(21)
+    deg = rng.integers(1, 33, size=n)
+    deg[rng.choice(n, 10, replace=False)] = rng.integers(80_000, 120_000, size=10)
+    src = np.repeat(np.arange(n), deg)
+    dst = rng.integers(0, n, size=src.size)
+    return gg.csr_from_edges(n, src, dst, weights=rng.integers(1, 256, size=src.size), symmetrize=False,
+                             dedup=False, drop_self_loops=False, sort=False, name="store-skew")
+
+
+def _store_bytes(g, bound):
+    deg = g.degrees()
+    sel = (deg >= 1) & (deg <= bound)
+    return g.n * 4 + int(((deg[sel] + 3) // 4 * 4).sum()) * 8  # index + ids + weights, 4-entry aligned
+
+
+def test_store_bound_rule_and_budget():
+    """The short-list store takes lists of up to 32 entries on a graph whose
+    short lists hold few of its entries and up to 16 on a uniform one; with
+    a device budget too small for it the bound drops to 16 and then to no
+    store, the load succeeds, and every result equals the oracle's with the
+    bytes read from the edge list counted by the bound."""
+    g = graph("urand14")
+    with E.load_graph(g, placement="host") as h:
+        assert h.store_bound == expected_store_bound(g, h) == 16
+    g = store_skew_graph()
+    with E.load_graph(g, placement="device") as h:
+        assert h.store_bound == expected_store_bound(g, h) == 0
+    deg = g.degrees()
+    srcs = [gg.max_degree_vertex(g), int(np.flatnonzero(deg == 20)[0])]
+    exp_d = {s: oracle.sssp_g(g, s) for s in srcs}
+    exp_l = {s: oracle.bfs_g(g, s) for s in srcs}
+    before = E.device_bytes_in_use()
+    with E.load_graph(g, placement="host") as h:
+        assert h.store_bound == expected_store_bound(g, h) == 32
+        base = E.device_bytes_in_use() - before - _store_bytes(g, 32)  # row offsets and list heads
+    # one handle's work buffers, as the library reserves them, with room to spare
+    work = 6 * g.n * 4 + (g.n // 16 + 1) * 16 + min(g.n, g.m // 497 + 1) * 20 + 4096
+    budgets = {32: 0, 16: before + base + work + _store_bytes(g, 16),
+               0: before + base + work + _store_bytes(g, 16) - 8192}
+    assert _store_bytes(g, 32) - _store_bytes(g, 16) > 8192
+    try:
+        for bound, budget in budgets.items():
+            E.set_device_budget(budget)
+            with E.load_graph(g, placement="host") as h:
+                assert h.store_bound == bound, budget
+                for s in srcs:
+                    d, st = E.sssp(h, s)
+                    np.testing.assert_array_equal(d, exp_d[s], err_msg=f"bound={bound} src={s}")
+                    lv, st = E.bfs(h, s, top_down_only=True)
+                    np.testing.assert_array_equal(lv, exp_l[s], err_msg=f"bound={bound} src={s}")
+                    short = int(deg[(lv != E.INF) & (deg >= 1) & (deg <= bound)].sum())
+                    assert st["edges_scanned"] == oracle.reached_edges(g.offsets, lv)
+                    assert st["edge_bytes"] == 8 * (st["edges_scanned"] - short)
+            E.set_device_budget(0)
+    finally:
+        E.set_device_budget(0)
+    assert E.device_bytes_in_use() == before
+
 def test_stats_are_consistent():
     g = graph("kron16")
     s = gg.max_degree_vertex(g)
@@ -396,8 +458,9 @@ def test_stats_are_consistent():
         lv, st = E.bfs(h, s, time_kernels=True, top_down_only=True)
         reached = oracle.reached_edges(g.offsets, lv)
         assert st["edges_scanned"] == reached  # BFS expands each reached vertex once
-        # lists of at most 16 entries come from the short-list store in GPU memory
-        short = int(deg[(lv != E.INF) & (deg <= 16)].sum())
+        # lists of at most store_bound entries come from the short-list store in GPU memory
+        assert h.store_bound == expected_store_bound(g, h)
+        short = int(deg[(lv != E.INF) & (deg >= 1) & (deg <= h.store_bound)].sum())
         assert st["edge_bytes"] == 8 * (reached - short)
         assert st["iterations"] == int(lv[lv != E.INF].max()) + 1
         assert st["expand_launches"] == st["iterations"]
@@ -658,6 +721,16 @@ def test_borrowed_managed_arrays():
     assert ei.value.status == E.E_ARG and "cudaMallocManaged" in str(ei.value)
 
 
+def expected_store_bound(g, h):
+    """The short-list store's bound for a graph loaded with heads, without a
+    device budget: 32 when the lists of 1..32 entries hold at most 1/8 of
+    the entries, else 16 (0 for graphs in GPU memory)."""
+    if h.placement == "device":
+        return 0
+    deg = g.degrees()
+    return 32 if int(deg[(deg >= 1) & (deg <= 32)].sum()) * 8 <= g.m else 16
+
+
 def short_lists_graph(n=20000):
     """Lists of 0 to 19 entries (those of at most 16 are read whole from the
     short-list store in GPU memory, the others from the edge list), every
@@ -697,7 +770,8 @@ def test_short_lists_from_heads_sssp_bfs(placement, ids32):
                 lv, st = E.bfs(h, s, top_down_only=True)
                 exp = oracle.bfs_g(g, s)
                 np.testing.assert_array_equal(lv, exp, err_msg=f"heads={heads} src={s}")
-                if heads:  # every reached list of <= 16 entries came from the store
-                    short = int(deg[(exp != E.INF) & (deg <= 16)].sum())
+                assert h.store_bound == (expected_store_bound(g, h) if heads else 0)
+                if heads:  # every reached list of 1..store_bound entries came from the store
+                    short = int(deg[(exp != E.INF) & (deg >= 1) & (deg <= h.store_bound)].sum())
                     assert st["edges_scanned"] * (4 if ids32 else 8) - st["edge_bytes"] == \
                         short * (4 if ids32 else 8)
