@@ -58,6 +58,9 @@ def parse():
                     help="kron27 = the default line (Kronecker scale 27, edge factor 32, edges and weights "
                          "pinned in place in host memory, 16 GiB device budget); urand24 = uniform 2^24, "
                          "degree 32 (the c2 workload) as the headline")
+    ap.add_argument("--graph-cache", default=os.environ.get("EMOGI_GRAPH_CACHE"),
+                    help="directory of binary CSR files (graphgen.cached): the scale-27 graph is read from there "
+                         "when present, else generated and written there; default: generate, write nothing")
     ap.add_argument("--no-variants", action="store_true", help="skip the managed / access-pattern comparisons")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -95,13 +98,17 @@ def read_kron27_sources():
     return info
 
 
-def make_kron27():
+def make_kron27(cache_dir=None):
     """The scale-27 graph on huge pages and its 16 giant-component sources
     (the stored list when it belongs to this graph, else 16 seeded vertices
-    of degree >= 2, and the config says so)."""
+    of degree >= 2, and the config says so); with `cache_dir`, read from the
+    binary CSR cache there (written on first use)."""
     import graphgen as gg
     t0 = time.perf_counter()
-    g = gg.kronecker(KRON27["scale"], KRON27["ef"], seed=GEN_SEED, weights=True)
+    if cache_dir:
+        g = gg.cached(cache_dir, "kron", KRON27["scale"], KRON27["ef"], seed=GEN_SEED, weights=True)
+    else:
+        g = gg.kronecker(KRON27["scale"], KRON27["ef"], seed=GEN_SEED, weights=True)
     gen_s = time.perf_counter() - t0
     info = read_kron27_sources()
     if info.get("n") == g.n and info.get("m") == g.m and len(info.get("sources", [])) == N_SOURCES:
@@ -109,7 +116,8 @@ def make_kron27():
     else:
         srcs = [int(s) for s in gg.random_sources(g, N_SOURCES, seed=SRC_SEED, min_degree=2)]
         how = "16 seeded vertices of degree >= 2 (no stored giant-component list for this graph)"
-    return g, srcs, {"generation_s": round(gen_s, 1), "sources_from": how}
+    return g, srcs, {"generation_s": round(gen_s, 1), "sources_from": how,
+                     "graph_cache": bool(cache_dir)}
 
 
 def make_urand24(n=URAND24["n"], degree=URAND24["degree"]):
@@ -514,7 +522,7 @@ def ours(args):
     # on GB300: made after the CUDA context and a pinned probe buffer, the
     # same edge list got SSSP 5.7 s instead of 1.65 s.
     if args.workload == "kron27":
-        g, srcs, ginfo = make_kron27()
+        g, srcs, ginfo = make_kron27(args.graph_cache)
         ginfo["huge_pages"] = gg.huge_page_report()
         ginfo["numa"] = gg.numa_report(g.cols, g.weights)
     else:

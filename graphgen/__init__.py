@@ -386,3 +386,147 @@ def random_sources(g: Graph, count: int, seed: int = 2, min_degree: int = 1) -> 
 
 def num_threads() -> int:
     return int(_lib().gg_num_threads())
+
+
+# ------------------------------------------------------------ binary CSR cache
+# A generated graph is written once as one binary file and read back instead of
+# being generated again.  Layout (little-endian): a 64-byte header
+#   magic "EMOGICSR", format version u32, flags u32 (bit 0: weights, bit 1:
+#   undirected), n u64, m u64, name length u32, 28 reserved bytes,
+# the name (UTF-8), zero padding to a 4096-byte boundary, then offsets
+# uint64[n+1], cols uint64[m] and weights uint32[m], each starting on a
+# 4096-byte boundary, so that every array is read straight into its
+# (huge-page) destination.
+CACHE_MAGIC = b"EMOGICSR"
+CACHE_VERSION = 1
+# bumped whenever the generators' output for given arguments changes, so that a
+# cache written by an older builder is never read for a newer one
+GENERATOR_VERSION = 1
+_CACHE_ALIGN = 4096
+_CACHE_CHUNK = 1 << 28
+
+
+def _cache_layout(n: int, m: int, weights: bool, name: bytes):
+    def up(x):
+        return (x + _CACHE_ALIGN - 1) // _CACHE_ALIGN * _CACHE_ALIGN
+    off_at = up(64 + len(name))
+    cols_at = up(off_at + (n + 1) * 8)
+    w_at = up(cols_at + m * 8)
+    end = w_at + (m * 4 if weights else 0)
+    return off_at, cols_at, w_at, end
+
+
+def _io_ranges(start: int, nbytes: int):
+    return [(start + a, min(_CACHE_CHUNK, nbytes - a)) for a in range(0, nbytes, _CACHE_CHUNK)]
+
+
+def _parallel_io(fd: int, jobs, write: bool):
+    """jobs: (numpy byte view, file offset); chunks of 256 MiB on a thread pool
+    (the system calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def one(job):
+        view, at = job
+        done = 0
+        while done < view.nbytes:
+            mv = memoryview(view[done:])
+            k = os.pwrite(fd, mv, at + done) if write else os.preadv(fd, [mv], at + done)
+            if k <= 0:
+                raise OSError(f"short {'write' if write else 'read'} at byte {at + done}")
+            done += k
+
+    pieces = []
+    for arr, at in jobs:
+        b = arr.view(np.uint8).reshape(-1)
+        for a, k in _io_ranges(0, b.nbytes):
+            pieces.append((b[a:a + k], at + a))
+    with ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
+        list(ex.map(one, pieces))
+
+
+def save(g: Graph, path: str) -> None:
+    """Write `g` to `path` in the cache format (through a temporary file that
+    is renamed into place, so a reader never sees a partial file)."""
+    name = (g.name or "").encode()
+    n, m, has_w = int(g.n), int(g.m), g.weights is not None
+    off_at, cols_at, w_at, end = _cache_layout(n, m, has_w, name)
+    head = bytearray(64)
+    head[0:8] = CACHE_MAGIC
+    flags = (1 if has_w else 0) | (2 if g.undirected else 0)
+    head[8:36] = np.array([CACHE_VERSION, flags], "<u4").tobytes() + np.array([n, m], "<u8").tobytes() + \
+        np.array([len(name)], "<u4").tobytes()
+    tmp = f"{path}.tmp{os.getpid()}"
+    fd = os.open(tmp, os.O_WRONLY | os.O_CREAT | os.O_TRUNC, 0o644)
+    try:
+        os.ftruncate(fd, end)
+        os.pwrite(fd, bytes(head) + name, 0)
+        jobs = [(np.ascontiguousarray(g.offsets, dtype=np.uint64), off_at),
+                (np.ascontiguousarray(g.cols, dtype=np.uint64), cols_at)]
+        if has_w:
+            jobs.append((np.ascontiguousarray(g.weights, dtype=np.uint32), w_at))
+        _parallel_io(fd, jobs, write=True)
+        os.fsync(fd)
+    except BaseException:
+        os.close(fd)
+        os.unlink(tmp)
+        raise
+    os.close(fd)
+    os.replace(tmp, path)
+
+
+def load(path: str) -> Graph:
+    """Read a graph written by :func:`save`.  The edge list and weights land
+    in fresh arrays from :func:`aligned_empty` (huge pages from 1 GiB up), as
+    if generated.  Raises ValueError on a file that is not a cache of this
+    format or whose size does not match its header."""
+    fd = os.open(path, os.O_RDONLY)
+    try:
+        head = os.pread(fd, 64, 0)
+        if len(head) != 64 or head[0:8] != CACHE_MAGIC:
+            raise ValueError(f"{path}: not a graph cache file")
+        version, flags = np.frombuffer(head[8:16], "<u4")
+        n, m = (int(x) for x in np.frombuffer(head[16:32], "<u8"))
+        name_len = int(np.frombuffer(head[32:36], "<u4")[0])
+        if int(version) != CACHE_VERSION:
+            raise ValueError(f"{path}: cache format {int(version)}, expected {CACHE_VERSION}")
+        has_w = bool(flags & 1)
+        name = os.pread(fd, name_len, 64).decode()
+        off_at, cols_at, w_at, end = _cache_layout(n, m, has_w, name.encode())
+        if os.fstat(fd).st_size != end:
+            raise ValueError(f"{path}: {os.fstat(fd).st_size} bytes, the header describes {end}")
+        off = aligned_empty(n + 1, np.uint64)
+        cols = aligned_empty(m, np.uint64)
+        w = aligned_empty(m, np.uint32) if has_w else None
+        jobs = [(off, off_at), (cols, cols_at)] + ([(w, w_at)] if has_w else [])
+        _parallel_io(fd, jobs, write=False)
+    finally:
+        os.close(fd)
+    if int(off[0]) != 0 or int(off[-1]) != m:
+        raise ValueError(f"{path}: row offsets do not run from 0 to m = {m}")
+    return Graph(n=n, offsets=off, cols=cols, weights=w, undirected=bool(flags & 2), name=name)
+
+
+def cache_key(kind: str, size: int, degree: float, seed: int, weights: bool, wseed: Optional[int] = None) -> str:
+    """File name of a generated graph: the generator, its arguments and the
+    generator version."""
+    w = f"_w{seed if wseed is None else wseed}" if weights else ""
+    return f"{kind}_{size}_{degree}_s{seed}{w}_g{GENERATOR_VERSION}.csr"
+
+
+def cached(cache_dir: str, kind: str, size: int, degree: float, seed: int = 1, weights: bool = False,
+           wseed: Optional[int] = None) -> Graph:
+    """The graph `kronecker(size, degree, ...)` (kind "kron") or
+    `uniform(size, degree, ...)` (kind "urand"), read from `cache_dir` when it
+    holds it, else generated and written there."""
+    if kind not in ("kron", "urand"):
+        raise ValueError(f"unknown generator {kind!r}")
+    path = os.path.join(cache_dir, cache_key(kind, size, degree, seed, weights, wseed))
+    if os.path.exists(path):
+        return load(path)
+    if kind == "kron":
+        g = kronecker(int(size), int(degree), seed=seed, weights=weights, wseed=wseed)
+    else:
+        g = uniform(int(size), degree, seed=seed, weights=weights, wseed=wseed)
+    os.makedirs(cache_dir, exist_ok=True)
+    save(g, path)
+    return g

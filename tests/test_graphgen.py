@@ -133,3 +133,64 @@ def test_release_host_range_frees_pages_of_a_large_array():
     released = gg.release_host_range(a, 1000, a.size - 1000)
     assert released > (1 << 29)
     assert a[0] == 7 and a[-1] == 7 and a[a.size // 2] == 0
+
+
+def _same_graph(a, b):
+    assert (a.n, a.m, a.undirected, a.name) == (b.n, b.m, b.undirected, b.name)
+    assert np.array_equal(a.offsets, b.offsets) and np.array_equal(a.cols, b.cols)
+    assert (a.weights is None) == (b.weights is None)
+    if a.weights is not None:
+        assert np.array_equal(a.weights, b.weights)
+
+
+def test_binary_cache_round_trip(tmp_path):
+    """Weighted and unweighted, directed and undirected, empty graphs read
+    back equal to what was written, with every array 4096-byte aligned."""
+    graphs = [gg.kronecker(11, 16, seed=4, weights=True), gg.uniform(3000, 5, seed=2),
+              gg.empty_graph(7),
+              gg.csr_from_edges(5, np.array([0, 0, 3, 4]), np.array([1, 1, 2, 0]), weights=np.array([9, 8, 7, 6]),
+                                symmetrize=False, dedup=False, drop_self_loops=False, sort=False, name="tiny")]
+    graphs[-1].undirected = False
+    for i, g in enumerate(graphs):
+        p = str(tmp_path / f"g{i}.csr")
+        gg.save(g, p)
+        h = gg.load(p)
+        _same_graph(g, h)
+        for arr in (h.offsets, h.cols) + ((h.weights,) if h.weights is not None else ()):
+            assert arr.ctypes.data % 4096 == 0
+    assert not [f for f in os.listdir(tmp_path) if ".tmp" in f]
+
+
+def test_binary_cache_rejects_other_files(tmp_path):
+    g = gg.kronecker(10, 8, seed=1, weights=True)
+    p = str(tmp_path / "g.csr")
+    gg.save(g, p)
+    raw = open(p, "rb").read()
+    for bad, what in ((raw[:-4], "bytes"), (b"NOTACSR!" + raw[8:], "not a graph cache"),
+                      (raw[:8] + (9).to_bytes(4, "little") + raw[12:], "format")):
+        q = str(tmp_path / "bad.csr")
+        open(q, "wb").write(bad)
+        try:
+            gg.load(q)
+        except ValueError as e:
+            assert what in str(e)
+        else:
+            raise AssertionError(f"accepted a file with bad {what}")
+
+
+def test_cached_generates_once_then_reads(tmp_path, monkeypatch):
+    """The first call generates and writes, the second reads the file and
+    gets the same graph; other arguments get other files."""
+    d = str(tmp_path)
+    a = gg.cached(d, "kron", 10, 16, seed=5, weights=True)
+    _same_graph(a, gg.kronecker(10, 16, seed=5, weights=True))
+    calls = []
+    monkeypatch.setattr(gg, "kronecker", lambda *x, **k: calls.append(x))
+    b = gg.cached(d, "kron", 10, 16, seed=5, weights=True)
+    assert not calls
+    _same_graph(a, b)
+    monkeypatch.undo()
+    gg.cached(d, "kron", 10, 16, seed=6, weights=True)
+    gg.cached(d, "kron", 10, 16, seed=5)
+    gg.cached(d, "urand", 1000, 4, seed=5)
+    assert len(os.listdir(d)) == 4
