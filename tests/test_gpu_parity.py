@@ -725,7 +725,7 @@ def expected_store_bound(g, h):
     """The short-list store's bound for a graph loaded with heads, without a
     device budget: 32 when the lists of 1..32 entries hold at most 1/8 of
     the entries, else 16 (0 for graphs in GPU memory)."""
-    if h.placement == "device":
+    if h.placement == E.PLACE_DEVICE:
         return 0
     deg = g.degrees()
     return 32 if int(deg[(deg >= 1) & (deg <= 32)].sum()) * 8 <= g.m else 16
