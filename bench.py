@@ -66,14 +66,14 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the uniform 2^24 block and the multi-source, batched and serving measurements")
     ap.add_argument("--ncu-case", nargs="?", const="traversal", default=None,
-                    choices=["traversal", "msbfs", "batch", "pagerank", "kron", "access"],
+                    choices=["traversal", "msbfs", "batch", "pagerank", "kron", "access", "device"],
                     help="profiling case, then exit: 'traversal' = one BFS, SSSP and CC on a 2^22-vertex uniform "
                          "graph (1.1 GB edges in pinned host memory); 'kron' = the same on a Kronecker graph of "
                          "scale 23, edge factor 32 (2.2 GB edges in host memory); 'access' = top-down BFS on the "
                          "2^22 uniform graph with the naive, merged and merged+aligned reads; 'msbfs' = one "
                          "64-source pass on a scale-22 Kronecker graph in host memory; 'batch' = one batched BFS "
                          "over 128 uneven graphs in HBM; 'pagerank' = 3 PageRank iterations on the 2^22 uniform "
-                         "graph in host memory")
+                         "graph in host memory; 'device' = the 'traversal' calls with the graph in HBM")
     return ap.parse_args()
 
 
@@ -1039,10 +1039,15 @@ def ncu_case(args):
         print(json.dumps({"ncu_case": "top-down BFS, uniform n=2^22 degree 32, host, three access patterns",
                           **res}))
         return
+    placement = "host"
     if args.ncu_case == "kron":
         g = gg.kronecker(23, 32, seed=GEN_SEED, weights=True)
         srcs = [int(s) for s in gg.random_sources(g, 2, seed=SRC_SEED, min_degree=2)]
         what = f"Kronecker scale 23 ef 32 (m={g.m}), host placement"
+    elif args.ncu_case == "device":
+        g, srcs = make_urand24(1 << 22, URAND24["degree"])
+        placement = "device"
+        what = "uniform n=2^22 degree 32, device placement (edge list and weights in HBM)"
     else:
         g, srcs = make_urand24(1 << 22, URAND24["degree"])
         what = "uniform n=2^22 degree 32, host placement"
@@ -1051,7 +1056,7 @@ def ncu_case(args):
     def mark(what):  # separates the calls in a per-sweep trace (EMOGI_TRACE=1)
         print(f"=== {what}", file=sys.stderr, flush=True)
 
-    with E.load_graph(g, placement="host") as h:
+    with E.load_graph(g, placement=placement) as h:
         mark("bfs")
         sb = E.bfs(h, srcs[0], out=out)[1]
         mark("sssp")
