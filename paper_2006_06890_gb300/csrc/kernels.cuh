@@ -58,6 +58,7 @@ struct Sweep {
     const uint32_t* short_ids = nullptr;
     const uint32_t* short_w = nullptr;   // its weights (weighted graphs), or null
     uint32_t short_max = 0;              // longest list the store holds
+    uint32_t block_slices = 0;           // 1: each block walks its own contiguous slice of in_q
     unsigned long long* scanned_heads = nullptr;  // entries read from the store instead of the edge list
     uint64_t m = 0;                      // entries in the edge list (and weights): a lane's 16-byte
                                          // load at index j is whole when j + ids per load <= m
@@ -837,17 +838,33 @@ __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t k = c.in_q ? (uint64_t)*c.in_count : (uint64_t)c.all_n;
     unsigned long long scanned = 0, scanned_h = 0;
-    for (uint64_t base = warp * GPW; base < k; base += nwarps * GPW) {
+    // Which queue entries a group takes: by default the whole grid strides
+    // over the queue, so a group's successive lists lie nwarps * GPW entries
+    // apart.  With block_slices each block takes one contiguous slice of the
+    // queue and its warps stride within it, so that where the queue is in
+    // vertex order (runs of it, at least) a block's successive list reads stay
+    // close in the address space.  Measured on GB300 over a 96 GiB pinned host
+    // array: random 512-byte reads ran at 19.7 GB/s, the same reads at 4 KiB
+    // or 32 KiB spacing walked per block at 203-211 GB/s (the link's peak);
+    // the GPU's address translations reach 16 to 32 GiB of such an array.
+    uint64_t hi = k, first = warp * GPW, stride = nwarps * GPW;
+    if (c.block_slices && c.in_q) {
+        const uint64_t lo = k * blockIdx.x / gridDim.x;
+        hi = k * (blockIdx.x + 1) / gridDim.x;
+        first = lo + (threadIdx.x >> 5) * GPW;
+        stride = (blockDim.x >> 5) * GPW;
+    }
+    for (uint64_t base = first; base < hi; base += stride) {
         const uint64_t idx = base + grp;
         uint32_t v = 0;
         typename Op::S st = Op::kSkip;
-        if (idx < k) {
+        if (idx < hi) {
             v = c.in_q ? c.in_q[idx] : (uint32_t)idx;
             if (glane == 0) st = op.begin(v);
         }
         st = __shfl_sync(0xffffffffu, st, grp * G);
         uint64_t s = 0, e = 0;
-        if (idx < k && st != Op::kSkip) {
+        if (idx < hi && st != Op::kSkip) {
             s = c.off[v];
             e = c.off[v + 1];
         }

@@ -424,6 +424,7 @@ emogi_status build_sssp_exec(Ctx& c) {
     }
     dev::SsspFixed f;
     f.base = make_sweep(c, 0, false);
+    f.base.block_slices = ordered_frontier(c) ? 1u : 0u;  // the queue holds vertex-ordered runs
     f.q[0] = ws.q[0];
     f.q[1] = ws.q[1];
     f.qround = ws.qround;
@@ -623,6 +624,7 @@ emogi_status emogi_sssp(emogi_graph g, uint64_t src, uint32_t* dist, const emogi
         if (nk > 0 && !merge_tail) {
             EMOGI_TRY(reset_sweep_counters(c, side));
             Sweep s = make_sweep(c, side, false);
+            s.block_slices = ordered ? 1u : 0u;  // the queue holds vertex-ordered runs
             if (ordered) {
                 dev::SsspFlagsOp op{state, qround, ws.fflag, ws.xd, &ctr->far_min, &ctr->overflow, (uint32_t)T,
                                     sweeps, dev::INF, g->d_off, Th, ws.nflag};
