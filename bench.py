@@ -127,6 +127,27 @@ def make_urand24(n=URAND24["n"], degree=URAND24["degree"]):
     return g, [int(s) for s in srcs]
 
 
+def link_probe(E, cols, stream):
+    """Zero-copy read rates (GB/s) of this box over the borrowed edge list:
+    a streaming pass, 512-byte and 4 KiB blocks at random over the first GiB
+    and over the whole array, and 512-byte blocks spaced evenly with each
+    thread block walking its own region.  Random reads over a range beyond
+    what the GPU's address translations cover run far below the link's peak;
+    the same reads walked in address order do not."""
+    nb = cols.nbytes
+    one = min(nb, 1 << 30)
+    cases = {"stream_all": ("stream", 0, 0, nb), "random512_1GiB": ("random", 512, 1 << 21, one),
+             "random512_all": ("random", 512, 1 << 21, nb), "random4k_all": ("random", 4096, 1 << 18, nb),
+             "regions512_all": ("regions", 512, nb // 32768, nb)}
+    out = {}
+    for name, (pat, bb, blocks, rng) in cases.items():
+        ms = min(E.probe_host_reads(cols, pat, bb, blocks, nbytes=rng, stream=stream) for _ in range(2))
+        moved = rng // 16 * 16 if pat == "stream" else bb * blocks
+        out[name] = round(moved / ms / 1e6, 1)
+    out["unit"] = "GB/s"
+    return out
+
+
 def workload_config(workload, m):
     """The `config` of the bench line, the same for both arms (m = the graph's
     directed edge count)."""
@@ -555,6 +576,8 @@ def ours(args):
         factors = LINK_BYTES_PER_ALG_BYTE["urand"]
     ginfo["store_bound"] = h.store_bound  # lists of 1..store_bound entries are read from GPU memory
     link_peak = pinned_h2d_peak_gbs(torch)
+    if args.workload == "kron27":
+        ginfo["link_probe"] = link_probe(E, g.cols, stream)
 
     hl = headline(torch, E, h, g, srcs, stream, args, world, barrier)
     per = hl["per"]

@@ -407,6 +407,29 @@ int emogi_graph_placement(emogi_graph g);
  * list is read only over the link. */
 uint32_t emogi_graph_store_bound(emogi_graph g);
 
+/* Zero-copy read probe (a measurement aid with no counterpart among the
+ * paper's operations; Sec. 5.3 measures how zero-copy request patterns set
+ * the link's delivered bandwidth).  Times one kernel that reads the pinned,
+ * mapped host range [host, host + bytes) over the link:
+ *   EMOGI_PROBE_STREAM   the whole range, coalesced 16-byte loads
+ *   EMOGI_PROBE_RANDOM   `blocks` reads of block_bytes each, a warp per read,
+ *                        at pseudo-random block-aligned positions in the range
+ *   EMOGI_PROBE_REGIONS  `blocks` reads of block_bytes each, spaced evenly over
+ *                        the range (bytes / blocks apart); each thread block
+ *                        of the grid reads one contiguous share of them
+ *   host        16-byte aligned, pinned with cudaHostAlloc or cudaHostRegister
+ *               (e.g. a borrowed edge list while its graph is loaded); only read
+ *   cuda_stream stream to run on, or NULL for one the call creates
+ *   ms          receives the kernel's duration (CUDA events)
+ * The bytes read are `bytes` (rounded down to 16) for STREAM and
+ * block_bytes * blocks otherwise.  Errors: EMOGI_E_ARG (NULL pointers, a
+ * range under 16 bytes or not 16-byte aligned, memory that is not pinned and
+ * mapped, block_bytes not a multiple of 16 in [16, bytes], blocks == 0, or
+ * REGIONS blocks that do not fit apart), EMOGI_E_CUDA. */
+enum { EMOGI_PROBE_STREAM = 0, EMOGI_PROBE_RANDOM = 1, EMOGI_PROBE_REGIONS = 2 };
+emogi_status emogi_probe_host_reads(const void* host, uint64_t bytes, uint32_t pattern, uint32_t block_bytes,
+                                    uint64_t blocks, void* cuda_stream, double* ms);
+
 /* Static description of a status code. */
 const char* emogi_status_string(emogi_status s);
 

@@ -89,6 +89,7 @@ _SIGNATURES = [
     ("emogi_graph_num_edges", _U64, [_P]),
     ("emogi_graph_placement", _I32, [_P]),
     ("emogi_graph_store_bound", _U32, [_P]),
+    ("emogi_probe_host_reads", _I32, [_P, _U64, _U32, _U32, _U64, _P, ctypes.POINTER(ctypes.c_double)]),
     ("emogi_graph_share", _I32, [_P, ctypes.POINTER(_P)]),
     ("emogi_graph_workspace_bytes", _U64, [_P]),
     ("emogi_status_string", ctypes.c_char_p, [_I32]),
@@ -381,6 +382,20 @@ def msbfs(g: Graph, sources, out=None, **kw):
     s = Stats()
     _check(lib().emogi_msbfs(g.handle, srcs.ctypes.data, k, ptr, ctypes.byref(o), ctypes.byref(s)))
     return res, s.as_dict()
+
+
+PROBE_PATTERNS = {"stream": 0, "random": 1, "regions": 2}
+
+
+def probe_host_reads(arr: np.ndarray, pattern="stream", block_bytes=0, blocks=0, nbytes=None, stream=None) -> float:
+    """Milliseconds of one zero-copy read kernel over the pinned host array
+    `arr` (its first `nbytes` bytes): emogi_probe_host_reads."""
+    ms = ctypes.c_double()
+    nb = arr.nbytes if nbytes is None else int(nbytes)
+    st = int(getattr(stream, "cuda_stream", stream)) if stream is not None else None
+    _check(lib().emogi_probe_host_reads(arr.ctypes.data, nb, PROBE_PATTERNS[pattern], int(block_bytes), int(blocks),
+                                        st, ctypes.byref(ms)))
+    return ms.value
 
 
 def free_graph(g: Graph):

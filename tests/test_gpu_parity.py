@@ -775,3 +775,30 @@ def test_short_lists_from_heads_sssp_bfs(placement, ids32):
                     short = int(deg[(exp != E.INF) & (deg >= 1) & (deg <= h.store_bound)].sum())
                     assert st["edges_scanned"] * (4 if ids32 else 8) - st["edge_bytes"] == \
                         short * (4 if ids32 else 8)
+
+
+def test_host_read_probe():
+    """The zero-copy read probe times its three patterns over a borrowed edge
+    list while the graph is loaded, and rejects memory that is not pinned and
+    arguments whose reads would leave the range."""
+    g = graph("kron16")
+    cols = gg.aligned_empty(g.m, np.uint64)
+    cols[:] = g.cols
+    nb = cols.nbytes
+    with E.load_csr(g.n, g.m, g.offsets, cols, None, placement="host", borrow=True):
+        assert E.probe_host_reads(cols, "stream") > 0
+        assert E.probe_host_reads(cols, "random", 512, 4096) > 0
+        assert E.probe_host_reads(cols, "regions", 512, nb // 4096) > 0
+        assert E.probe_host_reads(cols, "regions", 16, nb // 16) > 0  # blocks back to back
+        assert E.probe_host_reads(cols, "random", nb // 16 * 16, 3) > 0  # one block spans the range
+        for args in (("random", 24, 10), ("random", 0, 10), ("random", 512, 0), ("regions", 512, 0),
+                     ("regions", 32, nb // 16), ("random", (nb // 16 + 1) * 16, 1)):
+            with pytest.raises(E.EmogiError) as ei:
+                E.probe_host_reads(cols, *args)
+            assert ei.value.status == E.E_ARG, args
+    with pytest.raises(E.EmogiError) as ei:  # unregistered again once the graph is freed
+        E.probe_host_reads(cols, "stream")
+    assert ei.value.status == E.E_ARG
+    with pytest.raises(E.EmogiError) as ei:
+        E.probe_host_reads(np.zeros(4096, np.uint64), "random", 512, 16)
+    assert ei.value.status == E.E_ARG
