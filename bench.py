@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--graph-cache", default=os.environ.get("EMOGI_GRAPH_CACHE"),
                     help="directory of binary CSR files (graphgen.cached): the scale-27 graph is read from there "
                          "when present, else generated and written there; default: generate, write nothing")
+    ap.add_argument("--link-reach", type=int, default=0, metavar="GIB",
+                    help="measure zero-copy read rates over a pinned huge-page host array of GIB GiB "
+                         "(emogi_probe_host_reads: streaming, random blocks over growing ranges, per-block "
+                         "regions), print one JSON line and exit")
     ap.add_argument("--no-variants", action="store_true", help="skip the managed / access-pattern comparisons")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
@@ -580,6 +584,13 @@ def ours(args):
         ginfo["link_probe"] = link_probe(E, g.cols, stream)
 
     hl = headline(torch, E, h, g, srcs, stream, args, world, barrier)
+    if args.workload == "kron27":
+        # the host memory behind the link is shared with the machine's other
+        # GPUs and tenants: a streaming pass right after the timed steps shows
+        # whether the link still delivered what the probe saw before them
+        nb = min(g.cols.nbytes, 8 << 30)
+        ms = min(E.probe_host_reads(g.cols, "stream", nbytes=nb, stream=stream) for _ in range(3))
+        ginfo["link_probe"]["stream_8GiB_after_timed_steps"] = round(nb / ms / 1e6, 1)
     per = hl["per"]
     launches = sum(s["kernel_launches"] for p in per for s in p)
     cfg = workload_config(args.workload, g.m)
@@ -1091,8 +1102,50 @@ def ncu_case(args):
     print(json.dumps({"ncu_case": what, "bfs": sb, "sssp": ss, "sssp_host_loop": sh, "cc": sc}))
 
 
+def link_reach(args):
+    """Zero-copy read rates over one pinned host array of args.link_reach GiB
+    on transparent huge pages: how far the GPU's address translations reach
+    for random reads, and what per-block address order recovers."""
+    import torch
+    import graphgen as gg
+    from paper_2006_06890_gb300 import _build
+    _build.build()
+    from paper_2006_06890_gb300 import emogi as E
+    nbytes = args.link_reach << 30
+    buf = gg.aligned_empty(nbytes // 8, np.uint64)
+    from concurrent.futures import ThreadPoolExecutor
+    gib = (1 << 30) // 8
+    with ThreadPoolExecutor(16) as ex:  # touch every page before it is pinned
+        list(ex.map(lambda i: buf[i * gib:(i + 1) * gib].fill(i), range(args.link_reach)))
+    cudart = torch.cuda.cudart()
+    torch.cuda.init()
+    if int(cudart.cudaHostRegister(buf.ctypes.data, nbytes, 2)) != 0:  # cudaHostRegisterMapped
+        raise RuntimeError("cudaHostRegister failed")
+    st = torch.cuda.Stream()
+    res = {"link_reach": f"pinned host array of {args.link_reach} GiB on huge pages", "unit": "GB/s",
+           "huge_pages": gg.huge_page_report()}
+    try:
+        def rate(pat, bb, blocks, rng, reps=2):
+            ms = min(E.probe_host_reads(buf, pat, bb, blocks, nbytes=rng, stream=st) for _ in range(reps))
+            moved = rng // 16 * 16 if pat == "stream" else bb * blocks
+            return round(moved / ms / 1e6, 1)
+        res["stream_1GiB"] = rate("stream", 0, 0, 1 << 30)
+        res["stream_all"] = rate("stream", 0, 0, nbytes)
+        ranges = [r for r in (1, 2, 4, 8, 16, 24, 32, 48, 64, 96, 128) if r <= args.link_reach]
+        for bb, blocks in ((128, 1 << 22), (512, 1 << 21), (4096, 1 << 18)):
+            res[f"random{bb}"] = {f"{r}GiB": rate("random", bb, blocks, r << 30) for r in ranges}
+        res["regions512"] = {f"every{sp // 1024}KiB": rate("regions", 512, nbytes // sp, nbytes)
+                             for sp in (4096, 32768, 262144)}
+    finally:
+        cudart.cudaHostUnregister(buf.ctypes.data)
+    print(json.dumps(res))
+
+
 def main():
     args = parse()
+    if args.link_reach:
+        link_reach(args)
+        return
     if args.ncu_case:
         ncu_case(args)
     elif args.impl == "reference":

@@ -1285,72 +1285,6 @@ __global__ void __launch_bounds__(256) k_expand_naive(Sweep c, Op op_in) {
     op.flush();
 }
 
-// Frontier compaction: appends the vertices whose flag byte is set to q and
-// clears the flags.  Each thread takes 16 flags (one 16-byte load), and each
-// block turns a run of consecutive flags into one run of the queue, in vertex
-// order (one atomicAdd per block and pass), so the sweep that reads the queue
-// walks the edge list in address order within each block's range.  A sweep
-// whose queue came from pushes in arrival order reads its lists at random
-// across the whole edge list; once that list exceeds what the GPU's address
-// translations cover (tens of GB of host memory), those reads ran 8x slower
-// (measured on GB300, uniform 2^26 vertices with 25.8 GB of ids + weights:
-// 21 GB/s in arrival order against 160 GB/s in vertex order).  Flags are
-// bytes set with plain stores: a bitmap needs an atomic OR per vertex, and on
-// a dense BFS level (14 M new vertices into a 2 MB bitmap) those contended.
-__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
-    const uint32_t m = __vcmpne4(x, 0u);  // 0xff in every non-zero byte
-    return ((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u);
-}
-
-__device__ __forceinline__ void compact_flags_body(uint8_t* flags, uint64_t nchunks, uint32_t* q, uint32_t* count,
-                                                   uint32_t cap) {
-    __shared__ uint32_t warp_off[32];
-    __shared__ uint32_t block_base;
-    uint4* chunks = reinterpret_cast<uint4*>(flags);
-    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    // every thread of a block runs the same number of passes (the bound is per block)
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < nchunks; base += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t ci = base + threadIdx.x;
-        uint4 w = make_uint4(0u, 0u, 0u, 0u);
-        if (ci < nchunks) w = chunks[ci];
-        uint32_t mask = nonzero_bytes(w.x) | (nonzero_bytes(w.y) << 4) | (nonzero_bytes(w.z) << 8) |
-                        (nonzero_bytes(w.w) << 12);
-        if (mask) chunks[ci] = make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t c = __popc(mask);
-        uint32_t incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= (uint32_t)o) incl += t;
-        }
-        if (lane == 31) warp_off[wid] = incl;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t tot = 0;
-            for (uint32_t i = 0; i < nw; i++) {
-                const uint32_t x = warp_off[i];
-                warp_off[i] = tot;
-                tot += x;
-            }
-            block_base = tot ? atomicAdd(count, tot) : 0u;
-        }
-        __syncthreads();
-        uint32_t pos = block_base + warp_off[wid] + incl - c;
-        while (mask) {
-            const uint32_t b = (uint32_t)__ffs((int)mask) - 1u;
-            mask &= mask - 1u;
-            if (pos < cap) q[pos] = (uint32_t)(ci * 16u + b);
-            pos++;
-        }
-        __syncthreads();  // warp_off and block_base are rewritten by the next pass
-    }
-}
-
-static __global__ void __launch_bounds__(256) k_compact_flags(uint8_t* flags, uint64_t nchunks, uint32_t* q,
-                                                              uint32_t* count, uint32_t cap) {
-    compact_flags_body(flags, nchunks, q, count, cap);
-}
-
 // Block-aggregated queue append for kernels whose blocks step through the
 // vertex range together: a block collects the ids its threads push in shared
 // memory and appends them with one atomicAdd per kBlockBuf/2 ids or so,
@@ -1393,6 +1327,95 @@ __device__ __forceinline__ void block_queue_push(BlockQueue& bq, uint32_t* q, ui
     if (cnt + blockDim.x > (uint32_t)kBlockBuf) block_queue_flush(bq, q, qcount, cap);
 }
 
+// Frontier compaction: appends the vertices whose flag byte is set to q and
+// clears the flags.  Each thread takes 16 flags (one 16-byte load); each block
+// takes one contiguous range of the flags and stages its ids in shared memory,
+// so that the queue is made of runs of up to kBlockBuf ids in vertex order
+// (one atomicAdd per run), and a sweep whose blocks each take a slice of the
+// queue walks the edge list in address order within each slice.  A sweep
+// whose queue came from pushes in arrival order reads its lists at random
+// across the whole edge list; once that list exceeds what the GPU's address
+// translations cover (tens of GB of host memory), those reads ran 8x slower
+// (measured on GB300, uniform 2^26 vertices with 25.8 GB of ids + weights:
+// 21 GB/s in arrival order against 160 GB/s in vertex order).  Flags are
+// bytes set with plain stores: a bitmap needs an atomic OR per vertex, and on
+// a dense BFS level (14 M new vertices into a 2 MB bitmap) those contended.
+__device__ __forceinline__ uint32_t nonzero_bytes(uint32_t x) {
+    const uint32_t m = __vcmpne4(x, 0u);  // 0xff in every non-zero byte
+    return ((m >> 7) & 1u) | ((m >> 14) & 2u) | ((m >> 21) & 4u) | ((m >> 28) & 8u);
+}
+
+__device__ __forceinline__ void compact_flags_body(uint8_t* flags, uint64_t nchunks, uint32_t* q, uint32_t* count,
+                                                   uint32_t cap) {
+    __shared__ uint32_t warp_off[32];
+    __shared__ uint32_t pass_total, block_base;
+    __shared__ BlockQueue bq;
+    if (threadIdx.x == 0) bq.count = 0;
+    __syncthreads();
+    uint4* chunks = reinterpret_cast<uint4*>(flags);
+    const uint32_t lane = threadIdx.x & 31u, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    // block b takes one contiguous range of chunks; every thread of a block
+    // runs the same number of passes (the bounds are per block)
+    const uint64_t per = (nchunks + gridDim.x - 1) / gridDim.x;
+    const uint64_t b0 = (uint64_t)blockIdx.x * per;
+    const uint64_t lo = b0 < nchunks ? b0 : nchunks, hi = lo + per < nchunks ? lo + per : nchunks;
+    for (uint64_t base = lo; base < hi; base += blockDim.x) {
+        const uint64_t ci = base + threadIdx.x;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (ci < hi) w = chunks[ci];
+        uint32_t mask = nonzero_bytes(w.x) | (nonzero_bytes(w.y) << 4) | (nonzero_bytes(w.z) << 8) |
+                        (nonzero_bytes(w.w) << 12);
+        if (mask) chunks[ci] = make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t c = __popc(mask);
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += t;
+        }
+        if (lane == 31) warp_off[wid] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (uint32_t i = 0; i < nw; i++) {
+                const uint32_t x = warp_off[i];
+                warp_off[i] = tot;
+                tot += x;
+            }
+            pass_total = tot;
+        }
+        __syncthreads();
+        const uint32_t tot = pass_total;
+        if (bq.count + tot > (uint32_t)kBlockBuf) block_queue_flush(bq, q, count, cap);  // block-uniform
+        const bool direct = tot > (uint32_t)kBlockBuf;  // more than the buffer holds: straight to the queue
+        if (direct) {
+            if (threadIdx.x == 0) block_base = atomicAdd(count, tot);
+            __syncthreads();
+        }
+        uint32_t pos = (direct ? block_base : bq.count) + warp_off[wid] + incl - c;
+        while (mask) {
+            const uint32_t b = (uint32_t)__ffs((int)mask) - 1u;
+            mask &= mask - 1u;
+            const uint32_t id = (uint32_t)(ci * 16u + b);
+            if (direct) {
+                if (pos < cap) q[pos] = id;
+            } else {
+                bq.ids[pos] = id;
+            }
+            pos++;
+        }
+        __syncthreads();  // warp_off, pass_total and the buffer count are rewritten below / next pass
+        if (threadIdx.x == 0 && !direct) bq.count += tot;
+        __syncthreads();
+    }
+    block_queue_flush(bq, q, count, cap);
+}
+
+static __global__ void __launch_bounds__(256) k_compact_flags(uint8_t* flags, uint64_t nchunks, uint32_t* q,
+                                                              uint32_t* count, uint32_t cap) {
+    compact_flags_body(flags, nchunks, q, count, cap);
+}
+
 __device__ __forceinline__ void far_split_body(uint32_t n, uint32_t* fflag, const uint32_t* dist, const uint32_t* xd,
                                                uint32_t* qround, uint32_t T, uint32_t round, uint32_t* nq_out,
                                                uint32_t* ncount_out, uint32_t* kept, uint32_t* far_min) {
@@ -1400,11 +1423,16 @@ __device__ __forceinline__ void far_split_body(uint32_t n, uint32_t* fflag, cons
     if (threadIdx.x == 0) bq.count = 0;
     __syncthreads();
     uint32_t lmin = INF, lkept = 0;
-    // every thread of a block runs the same number of passes (the bound is per block)
-    for (uint64_t base = (uint64_t)blockIdx.x * blockDim.x; base < n; base += (uint64_t)gridDim.x * blockDim.x) {
+    // block b takes one contiguous range of vertices, so the near vertices it
+    // appends form runs in vertex order (see compact_flags_body); every thread
+    // of a block runs the same number of passes (the bounds are per block)
+    const uint64_t per = ((uint64_t)n + gridDim.x - 1) / gridDim.x;
+    const uint64_t b0 = (uint64_t)blockIdx.x * per;
+    const uint64_t lo = b0 < n ? b0 : n, hi = lo + per < n ? lo + per : n;
+    for (uint64_t base = lo; base < hi; base += blockDim.x) {
         const uint64_t v = base + threadIdx.x;
         bool near = false;
-        if (v < n && fflag[v]) {
+        if (v < hi && fflag[v]) {
             const uint32_t d = dist[v];
             if (d >= xd[v] || qround[v] == round) {
                 // already expanded with this distance, or already in the queue:
