@@ -846,7 +846,8 @@ __device__ __forceinline__ void expand_group_body(const Sweep& c, Op& op) {
     // close in the address space.  Measured on GB300 over a 96 GiB pinned host
     // array: random 512-byte reads ran at 19.7 GB/s, the same reads at 4 KiB
     // or 32 KiB spacing walked per block at 203-211 GB/s (the link's peak);
-    // the GPU's address translations reach 16 to 32 GiB of such an array.
+    // beyond 16 GiB of such an array, random reads are bound by the GPU's
+    // address translations.
     uint64_t hi = k, first = warp * GPW, stride = nwarps * GPW;
     if (c.block_slices && c.in_q) {
         const uint64_t lo = k * blockIdx.x / gridDim.x;
