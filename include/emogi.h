@@ -131,8 +131,8 @@ typedef struct {
     uint64_t edges_scanned; /* neighbour-list entries read by the expansion kernels */
     uint64_t edges_reached; /* sum of out-degrees of reached vertices (the TEPS numerator; m for CC) */
     uint64_t edge_bytes;    /* bytes of ids read from the edge list: the entries of edges_scanned not
-                               served by the list heads in GPU memory, * bytes per id (8, or 4 for
-                               emogi_load_csr32) */
+                               served by the short-list store in GPU memory (emogi_graph_store_bound),
+                               * bytes per id (8, or 4 for emogi_load_csr32) */
     uint64_t weight_bytes;  /* weights read from the weight array (SSSP): those entries * 4 */
     double ms;              /* device time of the traversal, CUDA events on the launch stream */
     double expand_ms;       /* with EMOGI_OPT_TIME_KERNELS: summed duration of expansion launches */
