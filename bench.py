@@ -70,14 +70,16 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the uniform 2^24 block and the multi-source, batched and serving measurements")
     ap.add_argument("--ncu-case", nargs="?", const="traversal", default=None,
-                    choices=["traversal", "msbfs", "batch", "pagerank", "kron", "access", "device"],
+                    choices=["traversal", "msbfs", "batch", "pagerank", "kron", "access", "device", "kron27"],
                     help="profiling case, then exit: 'traversal' = one BFS, SSSP and CC on a 2^22-vertex uniform "
                          "graph (1.1 GB edges in pinned host memory); 'kron' = the same on a Kronecker graph of "
                          "scale 23, edge factor 32 (2.2 GB edges in host memory); 'access' = top-down BFS on the "
                          "2^22 uniform graph with the naive, merged and merged+aligned reads; 'msbfs' = one "
                          "64-source pass on a scale-22 Kronecker graph in host memory; 'batch' = one batched BFS "
                          "over 128 uneven graphs in HBM; 'pagerank' = 3 PageRank iterations on the 2^22 uniform "
-                         "graph in host memory; 'device' = the 'traversal' calls with the graph in HBM")
+                         "graph in host memory; 'device' = the 'traversal' calls with the graph in HBM; "
+                         "'kron27' = SSSP on the scale-27 bench graph, device-driven then host-driven loop "
+                         "(for EMOGI_TRACE=1 per-sweep traces and one-pass launch lists only)")
     return ap.parse_args()
 
 
@@ -1072,6 +1074,26 @@ def ncu_case(args):
                 res[acc] = E.bfs(h, srcs[0], out=out, access=acc, top_down_only=True)[1]
         print(json.dumps({"ncu_case": "top-down BFS, uniform n=2^22 degree 32, host, three access patterns",
                           **res}))
+        return
+    if args.ncu_case == "kron27":
+        # the headline graph: for per-sweep traces (EMOGI_TRACE=1) and one-pass
+        # ncu launch lists only; a 100 GB host edge list is no case for
+        # multi-pass captures
+        g, srcs, _ = make_kron27(args.graph_cache)
+        E.set_device_budget(DEVICE_BUDGET)
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        st = torch.cuda.Stream()
+        h = E.load_csr(g.n, g.m, g.offsets, g.cols, g.weights, placement="host", undirected=True, borrow=True)
+        E.sssp(h, srcs[0], out=out, stream=st)  # first touch of the borrowed arrays
+        print("=== sssp", file=sys.stderr, flush=True)
+        ss = E.sssp(h, srcs[1], out=out, stream=st)[1]
+        print("=== sssp_host_loop", file=sys.stderr, flush=True)
+        sh = E.sssp(h, srcs[1], out=out, stream=st, host_loop=True)[1]
+        print("=== end", file=sys.stderr, flush=True)
+        bound = h.store_bound
+        h.free()
+        print(json.dumps({"ncu_case": f"Kronecker scale 27 ef 32 (m={g.m}), host placement (borrowed), "
+                                      "16 GiB device budget", "store_bound": bound, "sssp": ss, "sssp_host_loop": sh}))
         return
     placement = "host"
     if args.ncu_case == "kron":
