@@ -986,6 +986,22 @@ def oracle_step(g, src):
     return oracle.reached_edges(g.offsets, lv) + g.m, (t1 - t0, t2 - t1)
 
 
+def host_cpu():
+    """The host's core count and CPU model (lscpu's "Model name", else the
+    machine type)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.machine()}
+
+
 def cpu_baseline(workload="kron27"):
     """The oracle's BFS and CC, single-threaded, on a bounded sample."""
     g, srcs, desc = cpu_sample(workload)
@@ -993,7 +1009,7 @@ def cpu_baseline(workload="kron27"):
     tot = tb + tc
     return {"value": round(edges / tot / 1e9, 5), "unit": "GTEPS", "cores": 1, "kind": "oracle",
             "sample": f"BFS from vertex {srcs[0]} + union-find CC on {desc}; single-threaded C; "
-                      f"{tot:.1f} s (bfs {tb:.1f}, cc {tc:.1f})"}
+                      f"{tot:.1f} s (bfs {tb:.1f}, cc {tc:.1f})", "host": host_cpu()}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -1033,6 +1049,7 @@ def reference(args):
            "config": workload_config(args.workload, read_kron27_sources().get("m") if args.workload == "kron27"
                                      else g.m),
            "cpu_baseline": {"value": round(value, 5), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                            "host": host_cpu(),
                             "sample": f"{args.steps} steps, each the oracle's BFS from one seeded vertex + "
                                       f"union-find CC on {desc}; one step per process, {cores} processes "
                                       "in parallel"},

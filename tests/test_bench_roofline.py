@@ -69,3 +69,8 @@ def test_link_probe_rates():
     assert r["unit"] == "GB/s"
     # every case runs twice, each over at most the array
     assert len(E.calls) == 10 and all(c[3] <= nb for c in E.calls)
+
+
+def test_host_cpu_reports_cores_and_model():
+    h = bench.host_cpu()
+    assert h["nproc"] == os.cpu_count() and isinstance(h["cpu_model"], str) and h["cpu_model"]
